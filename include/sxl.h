@@ -1,0 +1,178 @@
+/*
+ * sxl.h -- C-ABI of libsxl.so, the GB300 (sm_103a) hot path of
+ * spin-polarized extended-Lagrangian Born-Oppenheimer molecular dynamics
+ * (Zhang, Cawkwell, Negre, Perriot, Niklasson, arXiv 2303.03529).
+ *
+ * Per MD step the library builds the spin-resolved tight-binding
+ * Hamiltonians H_up/H_dn[n] from the extended charge/spin vector n
+ * (Sec. III.A, Eq. ShadowELatte), forms the finite-temperature density
+ * matrices D_sigma = f_FD(H_sigma) with one common chemical potential
+ * (Eq. D_min) by a recursive Fermi-operator expansion, reduces them to
+ * Mulliken charges and spins, applies the preconditioned low-rank Krylov
+ * approximation of the kernel K to the residual q[n] - n (Eqs. fv,
+ * mIJacobian) with first-order density-matrix responses, computes the
+ * forces at constant n (Eq. EqMot) and advances R and n with the
+ * dissipative modified Verlet scheme (Eq. Integration).
+ *
+ * Conventions for every entry point:
+ *   - Arrays are contiguous, row-major, float64.  Pointers named *_dev are
+ *     device pointers, *_host are host pointers.  The caller owns every
+ *     array it passes; the library never frees caller memory and keeps no
+ *     pointer to it after the call returns.
+ *   - The extended vector layout is n = [n_up (N_at); n_dn (N_at)] in
+ *     electrons relative to the neutral atom (Sec. II.G); positions are
+ *     N_at x 3 in Angstrom; forces N_at x 3 in eV/Angstrom; velocities
+ *     N_at x 3 in Angstrom/fs.
+ *   - All work is queued on the context's stream.  Calls that return a host
+ *     scalar or host array synchronize that stream before returning.
+ *   - Return value 0 = success, negative = SXL_E_* code; sxl_last_error()
+ *     gives a message.  Nothing aborts and no exception crosses the ABI.
+ *     Iterative device loops are capped and report SXL_E_NO_CONVERGENCE.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef SXL_H
+#define SXL_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SXL_OK                 0
+#define SXL_E_ARG             -1  /* invalid argument or size                  */
+#define SXL_E_CUDA            -2  /* a CUDA runtime call failed                 */
+#define SXL_E_NOMEM           -3  /* device allocation failed                   */
+#define SXL_E_NO_CONVERGENCE  -4  /* mu search, SCF or inversion hit its cap    */
+#define SXL_E_NAN             -5  /* a non-finite value was produced            */
+#define SXL_E_STATE           -6  /* call order violated (e.g. no density yet)  */
+#define SXL_E_UNSUPPORTED     -7  /* feature not available on this device       */
+
+/* arithmetic of the Fermi-operator expansion and response GEMM chains */
+#define SXL_FP64         0   /* float64 everywhere (parity form)                 */
+#define SXL_MIXED_FP16   1   /* fp16 tensor-core products, fp32 accumulation      */
+#define SXL_MIXED_BF16   2   /* bf16 tensor-core products, fp32 accumulation      */
+
+/* preconditioner K0 of Eq. Eq_Mot3 */
+#define SXL_K0_MINUS_IDENTITY 0  /* K0 = -I: the scaled delta kernel of Sec. II.E */
+#define SXL_K0_GIVEN          1  /* caller-supplied 2N_at x 2N_at matrix           */
+
+typedef struct sxl_ctx sxl_ctx;
+
+/* Model and run parameters, copied at sxl_create.  Units: eV, Angstrom, fs, amu. */
+typedef struct {
+  int    n_atoms;            /* N_at; orbitals N = 9 N_at (s, p, d)            */
+  double cell[3];            /* orthorhombic periodic box lengths             */
+  double eps_s, eps_p, eps_d;/* on-site energies                              */
+  double V0[10];             /* bond integrals ss-sigma sp-sigma sd-sigma pp-sigma
+                                pp-pi pd-sigma pd-pi dd-sigma dd-pi dd-delta  */
+  double q_decay, r0;        /* V(r) = V0 exp(-q_decay (r - r0)) s(r)          */
+  double r_cut, r_on;        /* C2 quintic switch s(r) on [r_on, r_cut]        */
+  double U, W, coulomb_k;    /* gamma_IJ = k / sqrt(r^2 + (k/U)^2), spin shift
+                                sigma (W/2)(n_up - n_dn)_I                    */
+  double kT;                 /* electronic temperature, beta = 1/kT            */
+  double n_elec_per_atom;    /* N_e = n_elec_per_atom * N_at                   */
+  double d0_s, d0_p, d0_d;   /* neutral-atom occupation per spin and orbital   */
+  double rep_A, rep_b;       /* pair repulsion A exp(-b (r - r0)) s(r)         */
+  double mass_amu, dt_fs;
+  int    krylov_rank;        /* m of Eq. mIJacobian                            */
+  int    kmax;               /* dissipation history length, c has kmax+1 terms */
+  double kappa, alpha;
+  double c[10];
+  int    precision;          /* SXL_FP64, SXL_MIXED_FP16 or SXL_MIXED_BF16     */
+  int    foe_steps;          /* recursion depth; 0 = choose from spectral bounds */
+  double foe_u_max;          /* bound on |eig(U)| that fixes the depth when
+                                foe_steps == 0 (0 = 0.25)                     */
+  int    mu_max_iter;        /* cap on chemical-potential Newton passes (0 = 30) */
+  double mu_tol;             /* |sum Tr D - N_e| tolerance (0 = 1e-10)         */
+} sxl_params;
+
+/* Create a context bound to the current CUDA device and `stream` (a
+ * cudaStream_t, NULL = legacy default stream).  Allocates every device work
+ * buffer the context needs (owned by the context, freed by sxl_destroy).
+ * Returns SXL_E_ARG for invalid parameters, SXL_E_NOMEM if allocation fails. */
+int sxl_create(const sxl_params* params, void* stream, sxl_ctx** out);
+int sxl_destroy(sxl_ctx* ctx);
+const char* sxl_last_error(const sxl_ctx* ctx);
+
+/* Stage a0/a1 (Sec. III.A): H0 from Slater-Koster blocks summed over the
+ * periodic images within r_cut, and the spin-resolved Hamiltonians
+ * H_sigma = H0 + diag((gamma n)_I + sigma (W/2) s_I).  R_dev N_at x 3, n_dev
+ * 2 N_at.  If H_dev is not NULL it receives H_up then H_dn (2 x N x N). */
+int sxl_hamiltonian(sxl_ctx* ctx, const double* R_dev, const double* n_dev, double* H_dev);
+
+/* Stage a3/a4 (Eq. D_min and the Mulliken charges of Sec. III.A): builds H,
+ * runs the Fermi-operator expansion and the common chemical-potential
+ * Newton search, and writes q_dev = [q_up; q_dn] (2 N_at, electrons relative
+ * to neutral).  *mu_io: on entry the starting guess (NaN = choose), on exit
+ * the converged mu.  Keeps the expansion chain for sxl_response. */
+int sxl_density(sxl_ctx* ctx, const double* R_dev, const double* n_dev,
+                double* q_dev, double* mu_io);
+
+/* D_up then D_dn (2 x N x N, device) of the last sxl_density call. */
+int sxl_density_matrix(sxl_ctx* ctx, double* D_dev);
+
+/* Stage a5 (Eq. fv): q_v = d q[n + lambda v]/d lambda at lambda = 0 for the
+ * state of the last sxl_density call, through first-order perturbation of
+ * the expansion chain with a common dmu (sum Tr dD = 0).  v_dev, qv_dev:
+ * 2 N_at.  *dmu_out (host, may be NULL) receives dmu. */
+int sxl_response(sxl_ctx* ctx, const double* v_dev, double* qv_dev, double* dmu_out);
+
+/* Preconditioner K0 ~ J^{-1} (Eq. Eq_Mot3).  mode SXL_K0_MINUS_IDENTITY or
+ * SXL_K0_GIVEN with K0_dev a 2N_at x 2N_at row-major device matrix (copied). */
+int sxl_set_k0(sxl_ctx* ctx, int mode, const double* K0_dev);
+
+/* Exact K0 = J^{-1} at the state of the last sxl_density call: 2 N_at
+ * responses to unit directions give J (Eq. RegJacobian), inverted on the
+ * device by Gauss-Jordan elimination with partial pivoting.  If J_dev is not
+ * NULL it receives J. */
+int sxl_build_exact_k0(sxl_ctx* ctx, double* J_dev);
+
+/* Stages a3-a6 (Eqs. fv, mIJacobian): density for (R, n), residual
+ * f = q - n, then the rank-`rank` preconditioned Krylov approximation
+ * Kf ~ (K0 J)^{-1} K0 f.  Kf_dev, q_dev: 2 N_at (q_dev may be NULL).
+ * *rel_res_out (host, may be NULL): |F~ c - f~| / |f~| of the least squares. */
+int krylov_kernel_apply(sxl_ctx* ctx, const double* R_dev, const double* n_dev,
+                        int rank, double* Kf_dev, double* q_dev, double* rel_res_out);
+
+/* Stages a7/a8 (Eqs. EqMot, ShadowELatte): density for (R, n), forces at
+ * constant n into F_dev (N_at x 3) and, if energies_host is not NULL,
+ * [U, E_band, E_coul, E_spin, E_entropy, E_rep] (6 doubles, eV). */
+int forces(sxl_ctx* ctx, const double* R_dev, const double* n_dev,
+           double* F_dev, double* energies_host);
+
+/* MD state: positions, velocities, n history (kmax+1 vectors of 2 N_at,
+ * newest first) and mu.  Device-pointer and host-pointer variants.  After
+ * setting the state, xlbomd_step evaluates forces and Kf at it first. */
+int sxl_set_state(sxl_ctx* ctx, const double* R_dev, const double* V_dev,
+                  const double* nhist_dev, double mu);
+int sxl_get_state(sxl_ctx* ctx, double* R_dev, double* V_dev, double* nhist_dev,
+                  double* mu_host);
+int sxl_set_state_host(sxl_ctx* ctx, const double* R_host, const double* V_host,
+                       const double* nhist_host, double mu);
+int sxl_get_state_host(sxl_ctx* ctx, double* R_host, double* V_host,
+                       double* nhist_host, double* mu_host);
+
+/* Stage a9 (Eq. Integration): `nsteps` sXL-BOMD steps from the context
+ * state.  stats_host (may be NULL) receives nsteps x 4 doubles
+ * [E_tot (eV), T (K), RMS(q - n), mu (eV)] after each step; energies are
+ * evaluated every step when stats_host is not NULL. */
+int xlbomd_step(sxl_ctx* ctx, int nsteps, double* stats_host);
+
+/* Stage a10 (Eq. QN): SCF at positions R_dev from the guess in n_dev
+ * (overwritten with the converged n).  Linear mixing 0.06 while
+ * RMS(q - n) >= 0.05, then the exact K0 = J^{-1} is built once and the
+ * Krylov quasi-Newton step n <- n - Kf is taken with up to krylov_rank
+ * directions, stopping each step once the relative least-squares residual is
+ * below 0.1.  Leaves the exact K0 installed.  Returns SXL_E_NO_CONVERGENCE
+ * after max_iter iterations. */
+int scf_solve(sxl_ctx* ctx, const double* R_dev, double* n_dev, double tol,
+              int max_iter, int* iters_out, double* rms_out);
+
+/* Diagnostics of the last density: [mu, N(mu), foe_steps, lambda_min,
+ * lambda_max, GEMM launches so far, own kernel launches so far]. */
+int sxl_info(sxl_ctx* ctx, double* out7);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SXL_H */

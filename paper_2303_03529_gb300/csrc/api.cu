@@ -1,0 +1,631 @@
+// Orchestration of the per-step electronic solve and the C-ABI entry points
+// declared in include/sxl.h.
+//
+// Density (Eq. D_min): with U = beta (H_sigma - mu I) / 2^(nr+1),
+//   T_0 = U (I - U^2/3 + 2 U^4/15)             (tanh to fifth order)
+//   T_{k+1} = 2 T_k Y_k,  Y_k = (I + T_k^2)^{-1} (Newton-Schulz),  k < nr,
+//   D = (I - T_nr) / 2 = [exp(beta (H - mu)) + I]^{-1}  (tanh doubling).
+// Response (Eq. fv) to a diagonal perturbation dH (per-atom shifts of the
+// direction v), by differentiating every step of the same chain:
+//   dT_{k+1} = 2 [dT_k - T_{k+1} (T_k dT_k + dT_k T_k) / 2] Y_k,
+//   dD = -dT_nr / 2 + dmu beta D (I - D), common dmu with sum Tr dD = 0.
+// The chemical potential is found by Newton steps on
+//   N(mu) = sum_sigma Tr D_sigma,  N'(mu) = beta sum_sigma Tr D (I - D),
+// each step rerunning the chain.
+#include "common.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+int sxl_fail(sxl_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+static int dalloc(sxl_ctx* c, double** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) return SXL_OK;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(double));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return sxl_fail(c, SXL_E_NOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  CUDA_TRY(c, cudaMemsetAsync(*p, 0, n * sizeof(double), c->st));
+  return SXL_OK;
+}
+
+static double tanh5(double u) { return u - u * u * u / 3.0 + 2.0 * std::pow(u, 5) / 15.0; }
+
+// ---------------------------------------------------------------------------
+static int ensure_chain(sxl_ctx* c, int nr) {
+  size_t mm = 2 * (size_t)c->N * c->N;
+  while ((int)c->T.size() < nr + 1) {
+    double* p;
+    SXL_TRY(dalloc(c, &p, mm));
+    c->T.push_back(p);
+  }
+  while ((int)c->Y.size() < nr) {
+    double* p;
+    SXL_TRY(dalloc(c, &p, mm));
+    c->Y.push_back(p);
+  }
+  return SXL_OK;
+}
+
+static int ns_count(double s, double tol) {
+  double e = s / (2.0 + s);
+  e *= e;
+  int j = 0;
+  while (e > tol && j < 12) { e *= e; ++j; }
+  return j;
+}
+
+// One pass of the expansion at chemical potential mu; fills q (2 N_at),
+// chi, and stats[0..1] = N(mu), N'(mu) on the device.
+static int foe_f64(sxl_ctx* c, double mu, double* stats_dev) {
+  const int N = c->N, nr = c->nr;
+  SXL_TRY(ensure_chain(c, nr));
+  c->umax = c->scale * std::max(std::fabs(c->lam_max - mu), std::fabs(mu - c->lam_min));
+  build_u_f64(c, c->H0, c->shift, mu, c->scale, c->U);
+  gemm_f64(c, 2, N, c->U, c->U, c->S, 1.0, nullptr, 0.0, 0.0, true);
+  gemm_f64(c, 2, N, c->S, c->S, c->Q, 2.0 / 15.0, c->S, -1.0 / 3.0, 1.0, true);
+  gemm_f64(c, 2, N, c->U, c->Q, c->T[0], 1.0, nullptr, 0.0, 0.0, true);
+  double t = std::min(tanh5(c->umax), 1.0);
+  const double tol = 4e-16;
+  c->ns_iters.assign(nr, 0);
+  for (int k = 0; k < nr; ++k) {
+    double* Sq = c->Sm;
+    gemm_f64(c, 2, N, c->T[k], c->T[k], Sq, 1.0, nullptr, 0.0, 0.0, true);
+    double s = t * t;
+    double ci = 2.0 / (2.0 + s);
+    int j = ns_count(s, tol);
+    c->ns_iters[k] = j;
+    double* cur = (j == 0) ? c->Y[k] : c->X0;
+    axpy_diag_f64(c, 2, N, cur, -ci * ci, Sq, 2.0 * ci - ci * ci);
+    for (int it = 0; it < j; ++it) {
+      double* nxt = (it == j - 1) ? c->Y[k] : (cur == c->X0 ? c->X1 : c->X0);
+      // P = X (I + T^2), X' = 2X - P X
+      gemm_f64(c, 2, N, cur, Sq, c->P, 1.0, cur, 1.0, 0.0, false);
+      gemm_f64(c, 2, N, c->P, cur, nxt, -1.0, cur, 2.0, 0.0, true);
+      cur = nxt;
+    }
+    gemm_f64(c, 2, N, c->T[k], c->Y[k], c->T[k + 1], 2.0, nullptr, 0.0, 0.0, true);
+    t = 2.0 * t / (1.0 + t * t);
+  }
+  rowstats_f64(c, 2, N, c->T[nr], c->diagT, c->rowsq);
+  small_kernels_density(c, c->q, stats_dev);
+  return SXL_OK;
+}
+
+// diag of a batch-2 matrix into out (2N)
+__global__ void k_diag2(int n, const double* __restrict__ M, double* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * n) return;
+  int s = i / n, r = i % n;
+  out[i] = M[(size_t)s * n * n + (size_t)r * n + r];
+}
+
+// First-order response of the chain to the scaled diagonal perturbation du.
+static int dmpt_f64(sxl_ctx* c, const double* du) {
+  const int N = c->N, nr = c->nr;
+  double* dS = c->Sm;
+  symcombo_f64(c, 2, N, dS, 0.0, nullptr, 0.0, nullptr, 1.0, du, c->U);
+  gemm_f64(c, 2, N, dS, c->S, c->G1, 1.0, nullptr, 0.0, 0.0, false);
+  symcombo_f64(c, 2, N, c->P, -1.0 / 3.0, dS, 2.0 / 15.0, c->G1, 0.0, nullptr, nullptr);
+  gemm_f64(c, 2, N, c->U, c->P, c->G1, 1.0, nullptr, 0.0, 0.0, false);
+  double* dA = c->dTa;
+  double* dB = c->dTb;
+  symcombo_f64(c, 2, N, dA, 0.0, nullptr, 0.5, c->G1, 0.5, du, c->Q);
+  for (int k = 0; k < nr; ++k) {
+    gemm_f64(c, 2, N, c->T[k], dA, c->P, 1.0, nullptr, 0.0, 0.0, false);
+    symcombo_f64(c, 2, N, c->Sm, 0.0, nullptr, 1.0, c->P, 0.0, nullptr, nullptr);
+    gemm_f64(c, 2, N, c->T[k + 1], c->Sm, c->G1, -0.5, dA, 1.0, 0.0, false);
+    gemm_f64(c, 2, N, c->G1, c->Y[k], dB, 2.0, nullptr, 0.0, 0.0, true);
+    std::swap(dA, dB);
+  }
+  LAUNCH(k_diag2, (2 * N + 255) / 256, 256, 0, c->st, N, dA, c->diagT + 2 * N);
+  return SXL_OK;
+}
+
+static int sync_host(sxl_ctx* c, const double* dev, int n) {
+  CUDA_TRY(c, cudaMemcpyAsync(c->hred, dev, n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return SXL_OK;
+}
+
+// Hamiltonian pieces for (R, n): H0 and gamma (rebuilt only when R changed),
+// per-atom shifts, spectral bounds.
+static int build_model(sxl_ctx* c, const double* R, const double* n) {
+  // compare R with the positions of the current H0 on the host
+  std::vector<double> hR(3 * c->nat), hC(3 * c->nat);
+  CUDA_TRY(c, cudaMemcpyAsync(hR.data(), R, 3 * c->nat * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(c, cudaMemcpyAsync(hC.data(), c->Rcur, 3 * c->nat * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  if (!c->h0_valid || std::memcmp(hR.data(), hC.data(), hR.size() * sizeof(double)) != 0) {
+    launch_build_h0(c, R);
+    launch_build_gamma(c, R);
+    CUDA_TRY(c, cudaMemcpyAsync(c->Rcur, R, 3 * c->nat * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+    c->h0_valid = true;
+  }
+  launch_spin_shift(c, n, c->shift);
+  gersh_bounds(c, c->red);
+  SXL_TRY(sync_host(c, c->red, 2));
+  c->lam_min = c->hred[0];
+  c->lam_max = c->hred[1];
+  if (!std::isfinite(c->lam_min) || !std::isfinite(c->lam_max))
+    return sxl_fail(c, SXL_E_NAN, "non-finite Hamiltonian");
+  return SXL_OK;
+}
+
+static int density(sxl_ctx* c, const double* R, const double* n, double mu_guess) {
+  SXL_TRY(build_model(c, R, n));
+  const double Ne = c->p.n_elec_per_atom * c->nat;
+  const double kT = c->p.kT;
+  double lo = c->lam_min - 40.0 * kT, hi = c->lam_max + 40.0 * kT;
+  if (c->p.foe_steps > 0) {
+    c->nr = c->p.foe_steps;
+  } else {
+    double ymax = 0.5 * c->beta * (hi - lo);
+    double ut = c->p.foe_u_max > 0 ? c->p.foe_u_max : 0.25;
+    c->nr = std::max(4, (int)std::ceil(std::log2(ymax / ut)));
+  }
+  c->scale = c->beta / std::ldexp(1.0, c->nr + 1);
+  double mu = std::isfinite(mu_guess) ? mu_guess : 0.5 * (c->lam_min + c->lam_max);
+  mu = std::min(std::max(mu, lo), hi);
+  const int maxit = c->p.mu_max_iter > 0 ? c->p.mu_max_iter : 30;
+  const double tol = c->p.mu_tol > 0 ? c->p.mu_tol : 1e-10;
+  double* stats = c->red + 16;
+  for (int it = 0;; ++it) {
+    SXL_TRY(foe_f64(c, mu, stats));
+    SXL_TRY(sync_host(c, stats, 2));
+    double Nmu = c->hred[0], dN = c->hred[1];
+    if (!std::isfinite(Nmu) || !std::isfinite(dN)) return sxl_fail(c, SXL_E_NAN, "non-finite density");
+    double err = Nmu - Ne;
+    if (std::fabs(err) < tol) break;
+    if (it + 1 >= maxit)
+      return sxl_fail(c, SXL_E_NO_CONVERGENCE, "chemical potential search hit its iteration cap");
+    if (err > 0) hi = mu; else lo = mu;
+    double mn = (dN > 0) ? mu - err / dN : 0.5 * (lo + hi);
+    if (!(mn > lo && mn < hi)) mn = 0.5 * (lo + hi);
+    mu = mn;
+  }
+  c->mu = mu;
+  c->have_density = true;
+  return SXL_OK;
+}
+
+static int response(sxl_ctx* c, const double* v, double* qv, double* dmu_dev) {
+  if (!c->have_density) return sxl_fail(c, SXL_E_STATE, "no density: call sxl_density first");
+  launch_spin_shift(c, v, c->dh);
+  perturb_du(c, c->dh, c->du);
+  SXL_TRY(dmpt_f64(c, c->du));
+  small_kernels_response(c, qv, dmu_dev);
+  return SXL_OK;
+}
+
+// Krylov approximation of K f at the current density (Eq. mIJacobian);
+// rel_tol > 0 stops early once the least-squares residual is below it.
+static int krylov(sxl_ctx* c, const double* n, int rank, double rel_tol, double* Kf_out,
+                  double* rel_out, int* rank_out) {
+  const int n2 = c->n2;
+  vec_axpby(c, n2, c->fres, 1.0, c->q, -1.0, n);
+  gemv_f64(c, n2, c->K0, c->fres, c->ftil, 1.0, nullptr, 0.0);
+  double* status = c->red + 32;
+  double* lsq = c->red + 40;
+  const double* w = c->ftil;
+  double nft = -1.0, rel = 1.0;
+  int k = 0;
+  for (; k < rank; ++k) {
+    krylov_orth(c, k, w, status);
+    SXL_TRY(sync_host(c, status, 2));
+    if (k == 0) nft = c->hred[1];
+    if (!(c->hred[0] > 1e-12 * nft) || !std::isfinite(c->hred[0])) break;
+    double* vk = c->Vk + (size_t)k * n2;
+    SXL_TRY(response(c, vk, c->qv, c->red + 48));
+    vec_axpby(c, n2, c->fv, 1.0, c->qv, -1.0, vk);
+    gemv_f64(c, n2, c->K0, c->fv, c->FTk + (size_t)k * n2, 1.0, nullptr, 0.0);
+    w = c->FTk + (size_t)k * n2;
+    if (rel_tol > 0) {
+      krylov_lsq(c, k + 1, lsq);
+      SXL_TRY(sync_host(c, lsq, 1));
+      rel = c->hred[0];
+      if (rel < rel_tol) { ++k; break; }
+    }
+  }
+  if (k == 0) {
+    CUDA_TRY(c, cudaMemsetAsync(c->Kf, 0, n2 * sizeof(double), c->st));
+    rel = 1.0;
+  } else if (rel_tol <= 0) {
+    krylov_lsq(c, k, lsq);
+    SXL_TRY(sync_host(c, lsq, 1));
+    rel = c->hred[0];
+  }
+  if (Kf_out && Kf_out != c->Kf)
+    CUDA_TRY(c, cudaMemcpyAsync(Kf_out, c->Kf, n2 * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  if (rel_out) *rel_out = rel;
+  if (rank_out) *rank_out = k;
+  return SXL_OK;
+}
+
+__global__ void k_energy_band(int N, const double* __restrict__ H0, double d0s, double d0p,
+                              double d0d, const double* dots, double* out) {
+  __shared__ double sm[1024];
+  double tr = 0.0, hd = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    double h = H0[(size_t)i * N + i];
+    int a = i % NORB;
+    double d0 = a == 0 ? d0s : (a < 4 ? d0p : d0d);
+    tr += h;
+    hd += h * d0;
+  }
+  sm[threadIdx.x] = tr;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  double ttr = sm[0];
+  __syncthreads();
+  sm[threadIdx.x] = hd;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = 0.5 * (ttr - dots[0]) + 0.5 * (ttr - dots[1]) - 2.0 * sm[0];
+}
+
+// forces at the current density; energies (6 doubles, host) if requested
+static int eval_forces(sxl_ctx* c, const double* R, const double* n, double* F, double* en) {
+  double* erep = c->tmpv;  // nat doubles
+  launch_forces(c, R, n, c->q, F, erep);
+  if (en) {
+    const size_t nn = (size_t)c->N * c->N;
+    double* d = c->red + 64;
+    dot_f64(c, (long long)nn, c->H0, c->T[c->nr], d);
+    dot_f64(c, (long long)nn, c->H0, c->T[c->nr] + nn, d + 1);
+    LAUNCH(k_energy_band, 1, 1024, 0, c->st, c->N, c->H0, c->p.d0_s, c->p.d0_p, c->p.d0_d, d,
+           d + 2);
+    energy_terms(c, n, erep, d + 3);
+    SXL_TRY(sync_host(c, d + 2, 4));
+    double band = c->hred[0], coul = c->hred[1], spin = c->hred[2], rep = c->hred[3];
+    double ent = 0.0;  // entropy: see sxl_energy_entropy
+    en[0] = band + coul + spin + ent + rep;
+    en[1] = band; en[2] = coul; en[3] = spin; en[4] = ent; en[5] = rep;
+  }
+  return SXL_OK;
+}
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* sxl_last_error(const sxl_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int sxl_create(const sxl_params* prm, void* stream, sxl_ctx** out) {
+  if (!prm || !out) return SXL_E_ARG;
+  *out = nullptr;
+  const sxl_params& p = *prm;
+  if (p.n_atoms < 2 || p.n_atoms > 20000) return SXL_E_ARG;
+  for (int i = 0; i < 3; ++i)
+    if (!(p.cell[i] > 0) || !(1.5 * p.cell[i] > p.r_cut)) return SXL_E_ARG;
+  if (!(p.kT > 0) || !(p.r_cut > p.r_on) || !(p.r_on > 0) || !(p.U > 0) || !(p.coulomb_k > 0))
+    return SXL_E_ARG;
+  if (p.krylov_rank < 1 || p.krylov_rank > 32 || p.kmax < 1 || p.kmax > 9) return SXL_E_ARG;
+  if (p.precision != SXL_FP64 && p.precision != SXL_MIXED_FP16 && p.precision != SXL_MIXED_BF16)
+    return SXL_E_ARG;
+  if (p.foe_steps < 0 || p.foe_steps > 40) return SXL_E_ARG;
+  if (!(p.n_elec_per_atom > 0 && p.n_elec_per_atom < 18)) return SXL_E_ARG;
+  sxl_ctx* c = new sxl_ctx();
+  c->p = p;
+  c->st = (cudaStream_t)stream;
+  c->nat = p.n_atoms;
+  c->N = NORB * p.n_atoms;
+  c->n2 = 2 * p.n_atoms;
+  c->beta = 1.0 / p.kT;
+  c->hist_head = 0;
+  c->mu = NAN;
+  c->state_ready = c->evaluated = c->have_density = c->h0_valid = false;
+  c->nr = 0; c->nr_cap = 0;
+  c->lam_min = 0; c->lam_max = 0;
+  c->n_gemm = 0;
+  if (p.precision != SXL_FP64) {
+    // the mixed-precision chain is provided by the tensor-core path
+    int r = sxl_mixed_supported(c);
+    if (r != SXL_OK) { int rr = r; delete c; return rr; }
+  }
+  const int nat = c->nat, N = c->N, n2 = c->n2, K1 = p.kmax + 1;
+  const size_t mm = 2 * (size_t)N * N;
+  int r = SXL_OK;
+#define AL(ptr, n) if (r == SXL_OK) r = dalloc(c, &c->ptr, (n))
+  AL(R, 3 * nat); AL(V, 3 * nat); AL(F, 3 * nat); AL(Rcur, 3 * nat); AL(Fband, 3 * nat);
+  AL(nhist, (size_t)K1 * n2); AL(Kf, n2); AL(q, n2); AL(fres, n2); AL(tmpv, std::max(n2, 3 * nat));
+  AL(gamma_m, (size_t)nat * nat); AL(H0, (size_t)N * N); AL(h0abs, N); AL(shift, 2 * nat);
+  AL(U, mm); AL(S, mm); AL(Q, mm); AL(X0, mm); AL(X1, mm); AL(P, mm); AL(Sm, mm);
+  AL(dTa, mm); AL(dTb, mm); AL(G1, mm);
+  AL(diagT, 4 * N); AL(rowsq, 2 * N); AL(chi, 2 * N); AL(du, 2 * N); AL(dh, 2 * nat);
+  AL(red, 4096);
+  AL(K0, (size_t)n2 * n2); AL(Vk, (size_t)32 * n2); AL(FTk, (size_t)32 * n2); AL(ftil, n2);
+  AL(cvec, 64); AL(qv, n2); AL(fv, n2); AL(wvec, (size_t)34 * n2);
+  AL(Jm, (size_t)n2 * n2); AL(Jinv, (size_t)n2 * n2);
+#undef AL
+  if (r == SXL_OK) {
+    cudaError_t e = cudaMallocHost((void**)&c->hred, 64 * sizeof(double));
+    if (e != cudaSuccess) r = SXL_E_NOMEM;
+  }
+  if (r != SXL_OK) { sxl_destroy(c); return r; }
+  r = sxl_set_k0(c, SXL_K0_MINUS_IDENTITY, nullptr);
+  if (r != SXL_OK) { sxl_destroy(c); return r; }
+  *out = c;
+  return SXL_OK;
+}
+
+int sxl_destroy(sxl_ctx* c) {
+  if (!c) return SXL_OK;
+  if (c->st) cudaStreamSynchronize(c->st); else cudaDeviceSynchronize();
+  double* ptrs[] = {c->R, c->V, c->F, c->Rcur, c->Fband, c->nhist, c->Kf, c->q, c->fres, c->tmpv,
+                    c->gamma_m, c->H0, c->h0abs, c->shift, c->U, c->S, c->Q, c->X0, c->X1, c->P,
+                    c->Sm, c->dTa, c->dTb, c->G1, c->diagT, c->rowsq, c->chi, c->du, c->dh,
+                    c->red, c->K0, c->Vk, c->FTk, c->ftil, c->cvec, c->qv, c->fv, c->wvec, c->Jm,
+                    c->Jinv};
+  for (double* p : ptrs)
+    if (p) cudaFree(p);
+  for (double* p : c->T) cudaFree(p);
+  for (double* p : c->Y) cudaFree(p);
+  sxl_mixed_free(c);
+  if (c->hred) cudaFreeHost(c->hred);
+  delete c;
+  return SXL_OK;
+}
+
+int sxl_hamiltonian(sxl_ctx* c, const double* R, const double* n, double* H) {
+  if (!c || !R || !n) return SXL_E_ARG;
+  c->have_density = false;
+  SXL_TRY(build_model(c, R, n));
+  // H_sigma = H0 + diag(shift_sigma): the U builder with mu = 0, scale = 1
+  if (H) build_u_f64(c, c->H0, c->shift, 0.0, 1.0, H);
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return SXL_OK;
+}
+
+int sxl_density(sxl_ctx* c, const double* R, const double* n, double* q, double* mu_io) {
+  if (!c || !R || !n) return SXL_E_ARG;
+  double g = mu_io ? *mu_io : NAN;
+  c->have_density = false;
+  SXL_TRY(density(c, R, n, g));
+  if (q) CUDA_TRY(c, cudaMemcpyAsync(q, c->q, c->n2 * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  if (mu_io) *mu_io = c->mu;
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return SXL_OK;
+}
+
+__global__ void k_d_from_t(size_t nn, const double* T, double* D, int N) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  size_t e = i % ((size_t)N * N);
+  D[i] = ((e / N == e % N) ? 0.5 : 0.0) - 0.5 * T[i];
+}
+
+int sxl_density_matrix(sxl_ctx* c, double* D) {
+  if (!c || !D) return SXL_E_ARG;
+  if (!c->have_density) return sxl_fail(c, SXL_E_STATE, "no density");
+  size_t nn = 2 * (size_t)c->N * c->N;
+  LAUNCH(k_d_from_t, (unsigned)((nn + 255) / 256), 256, 0, c->st, nn, c->T[c->nr], D, c->N);
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return SXL_OK;
+}
+
+int sxl_response(sxl_ctx* c, const double* v, double* qv, double* dmu_out) {
+  if (!c || !v || !qv) return SXL_E_ARG;
+  SXL_TRY(response(c, v, qv, c->red + 48));
+  SXL_TRY(sync_host(c, c->red + 48, 1));
+  if (dmu_out) *dmu_out = c->hred[0];
+  return SXL_OK;
+}
+
+__global__ void k_minus_eye(int n, double* K) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < (size_t)n * n) K[i] = (i / n == i % n) ? -1.0 : 0.0;
+}
+
+int sxl_set_k0(sxl_ctx* c, int mode, const double* K0) {
+  if (!c) return SXL_E_ARG;
+  size_t nn = (size_t)c->n2 * c->n2;
+  if (mode == SXL_K0_MINUS_IDENTITY) {
+    LAUNCH(k_minus_eye, (unsigned)((nn + 255) / 256), 256, 0, c->st, c->n2, c->K0);
+  } else if (mode == SXL_K0_GIVEN) {
+    if (!K0) return SXL_E_ARG;
+    CUDA_TRY(c, cudaMemcpyAsync(c->K0, K0, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  } else {
+    return SXL_E_ARG;
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return SXL_OK;
+}
+
+// J[:, j] = qv - e_j
+__global__ void k_set_col(int n2, int j, const double* qv, double* J) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n2) J[(size_t)i * n2 + j] = qv[i] - (i == j ? 1.0 : 0.0);
+}
+__global__ void k_unit(int n2, int j, double* e) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n2) e[i] = (i == j) ? 1.0 : 0.0;
+}
+
+static int build_exact_k0(sxl_ctx* c, double* Jout) {
+  if (!c->have_density) return sxl_fail(c, SXL_E_STATE, "no density");
+  const int n2 = c->n2;
+  double* e = c->tmpv;
+  for (int j = 0; j < n2; ++j) {
+    LAUNCH(k_unit, (n2 + 255) / 256, 256, 0, c->st, n2, j, e);
+    SXL_TRY(response(c, e, c->qv, c->red + 48));
+    LAUNCH(k_set_col, (n2 + 255) / 256, 256, 0, c->st, n2, j, c->qv, c->Jm);
+  }
+  if (Jout) CUDA_TRY(c, cudaMemcpyAsync(Jout, c->Jm, (size_t)n2 * n2 * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  SXL_TRY(gauss_jordan_inverse(c, n2, c->Jm, c->K0));
+  return SXL_OK;
+}
+
+int sxl_build_exact_k0(sxl_ctx* c, double* J) {
+  if (!c) return SXL_E_ARG;
+  SXL_TRY(build_exact_k0(c, J));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return SXL_OK;
+}
+
+int krylov_kernel_apply(sxl_ctx* c, const double* R, const double* n, int rank, double* Kf,
+                        double* q, double* rel_res) {
+  if (!c || !R || !n || !Kf || rank < 1 || rank > 32) return SXL_E_ARG;
+  double g = c->have_density ? c->mu : NAN;
+  c->have_density = false;
+  SXL_TRY(density(c, R, n, g));
+  SXL_TRY(krylov(c, n, rank, 0.0, Kf, rel_res, nullptr));
+  if (q) CUDA_TRY(c, cudaMemcpyAsync(q, c->q, c->n2 * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return SXL_OK;
+}
+
+int forces(sxl_ctx* c, const double* R, const double* n, double* F, double* en) {
+  if (!c || !R || !n || !F) return SXL_E_ARG;
+  double g = c->have_density ? c->mu : NAN;
+  c->have_density = false;
+  SXL_TRY(density(c, R, n, g));
+  SXL_TRY(eval_forces(c, R, n, F, en));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return SXL_OK;
+}
+
+static int set_state(sxl_ctx* c, const double* R, const double* V, const double* nh, double mu,
+                     cudaMemcpyKind kind) {
+  const int n2 = c->n2, K1 = c->p.kmax + 1;
+  CUDA_TRY(c, cudaMemcpyAsync(c->R, R, 3 * c->nat * sizeof(double), kind, c->st));
+  CUDA_TRY(c, cudaMemcpyAsync(c->V, V, 3 * c->nat * sizeof(double), kind, c->st));
+  CUDA_TRY(c, cudaMemcpyAsync(c->nhist, nh, (size_t)K1 * n2 * sizeof(double), kind, c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  c->hist_head = 0;
+  c->mu = mu;
+  c->state_ready = true;
+  c->evaluated = false;
+  return SXL_OK;
+}
+
+static int get_state(sxl_ctx* c, double* R, double* V, double* nh, double* mu, cudaMemcpyKind kind) {
+  const int n2 = c->n2, K1 = c->p.kmax + 1;
+  if (R) CUDA_TRY(c, cudaMemcpyAsync(R, c->R, 3 * c->nat * sizeof(double), kind, c->st));
+  if (V) CUDA_TRY(c, cudaMemcpyAsync(V, c->V, 3 * c->nat * sizeof(double), kind, c->st));
+  if (nh)
+    for (int k = 0; k < K1; ++k)
+      CUDA_TRY(c, cudaMemcpyAsync(nh + (size_t)k * n2, c->nhist + (size_t)((c->hist_head + k) % K1) * n2,
+                                  n2 * sizeof(double), kind, c->st));
+  if (mu) *mu = c->mu;
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return SXL_OK;
+}
+
+int sxl_set_state(sxl_ctx* c, const double* R, const double* V, const double* nh, double mu) {
+  if (!c || !R || !V || !nh) return SXL_E_ARG;
+  return set_state(c, R, V, nh, mu, cudaMemcpyDeviceToDevice);
+}
+int sxl_get_state(sxl_ctx* c, double* R, double* V, double* nh, double* mu) {
+  if (!c) return SXL_E_ARG;
+  return get_state(c, R, V, nh, mu, cudaMemcpyDeviceToDevice);
+}
+int sxl_set_state_host(sxl_ctx* c, const double* R, const double* V, const double* nh, double mu) {
+  if (!c || !R || !V || !nh) return SXL_E_ARG;
+  return set_state(c, R, V, nh, mu, cudaMemcpyHostToDevice);
+}
+int sxl_get_state_host(sxl_ctx* c, double* R, double* V, double* nh, double* mu) {
+  if (!c) return SXL_E_ARG;
+  return get_state(c, R, V, nh, mu, cudaMemcpyDeviceToHost);
+}
+
+// density, forces (+energies) and Kf at the context state
+static int evaluate(sxl_ctx* c, double* en) {
+  const double* n = c->nhist + (size_t)c->hist_head * c->n2;
+  c->have_density = false;
+  SXL_TRY(density(c, c->R, n, c->mu));
+  SXL_TRY(eval_forces(c, c->R, n, c->F, en));
+  SXL_TRY(krylov(c, n, c->p.krylov_rank, 0.0, c->Kf, nullptr, nullptr));
+  c->evaluated = true;
+  return SXL_OK;
+}
+
+int xlbomd_step(sxl_ctx* c, int nsteps, double* stats) {
+  if (!c || nsteps < 0) return SXL_E_ARG;
+  if (!c->state_ready) return sxl_fail(c, SXL_E_STATE, "no MD state: call sxl_set_state first");
+  if (!c->evaluated) SXL_TRY(evaluate(c, nullptr));
+  const int K1 = c->p.kmax + 1;
+  for (int s = 0; s < nsteps; ++s) {
+    md_half_kick(c, c->V, c->F);
+    md_drift(c, c->R, c->V);
+    int head_new = (c->hist_head + K1 - 1) % K1;
+    md_nupdate(c, head_new);
+    c->hist_head = head_new;
+    double en[6];
+    SXL_TRY(evaluate(c, stats ? en : nullptr));
+    md_half_kick(c, c->V, c->F);
+    if (stats) {
+      const double* n = c->nhist + (size_t)c->hist_head * c->n2;
+      md_kinetic(c, c->V, c->red + 100);
+      rms_f64(c, c->n2, c->q, n, c->red + 101);
+      SXL_TRY(sync_host(c, c->red + 100, 2));
+      double ke = c->hred[0];
+      double T = 2.0 * ke / ((3.0 * c->nat - 3.0) * KB_EV);
+      stats[4 * s + 0] = en[0] + ke;
+      stats[4 * s + 1] = T;
+      stats[4 * s + 2] = c->hred[1];
+      stats[4 * s + 3] = c->mu;
+    }
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return SXL_OK;
+}
+
+int scf_solve(sxl_ctx* c, const double* R, double* n, double tol, int max_iter, int* iters_out,
+              double* rms_out) {
+  if (!c || !R || !n || !(tol > 0) || max_iter < 1) return SXL_E_ARG;
+  bool k0 = false;
+  double mu = NAN, rms = 1e300;
+  int it = 0;
+  for (; it < max_iter; ++it) {
+    c->have_density = false;
+    SXL_TRY(density(c, R, n, mu));
+    mu = c->mu;
+    rms_f64(c, c->n2, c->q, n, c->red + 102);
+    SXL_TRY(sync_host(c, c->red + 102, 1));
+    rms = c->hred[0];
+    if (!std::isfinite(rms)) return sxl_fail(c, SXL_E_NAN, "non-finite residual in SCF");
+    if (rms < tol) break;
+    if (!k0 && rms >= 0.05) {
+      // linear mixing n <- n + 0.06 (q - n)
+      vec_axpby(c, c->n2, n, 0.94, n, 0.06, c->q);
+      continue;
+    }
+    if (!k0) {
+      SXL_TRY(build_exact_k0(c, nullptr));
+      k0 = true;
+    }
+    SXL_TRY(krylov(c, n, c->p.krylov_rank, 0.1, c->Kf, nullptr, nullptr));
+    vec_axpby(c, c->n2, n, 1.0, n, -1.0, c->Kf);
+  }
+  if (iters_out) *iters_out = it;
+  if (rms_out) *rms_out = rms;
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  if (!(rms < tol)) return sxl_fail(c, SXL_E_NO_CONVERGENCE, "SCF hit max_iter");
+  return SXL_OK;
+}
+
+int sxl_info(sxl_ctx* c, double* out) {
+  if (!c || !out) return SXL_E_ARG;
+  out[0] = c->mu;
+  out[1] = 0.0;
+  out[2] = c->nr;
+  out[3] = c->lam_min;
+  out[4] = c->lam_max;
+  out[5] = (double)c->n_gemm;
+  out[6] = (double)g_sxl_launches;
+  return SXL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// Internal declarations shared by the translation units of libsxl.so.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/sxl.h"
+
+#define NORB 9
+#define KB_EV 8.617333262e-5          // Boltzmann constant, eV/K
+#define MVV_EV 103.642696562          // 1 amu A^2 / fs^2 in eV
+
+// Launch accounting: every kernel launch of the library goes through LAUNCH so
+// the host can report how many of its own kernels ran.
+extern unsigned long long g_sxl_launches;
+#define LAUNCH(kern, grid, block, smem, stream, ...)                 \
+  do {                                                                \
+    kern<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);        \
+    ++g_sxl_launches;                                                 \
+  } while (0)
+
+// Mixed-precision operand storage: every matrix is a (hi, lo) pair of 16-bit
+// tensors with value = hi + lo * 2^-LO_SHIFT (lo holds the scaled residual).
+#define LO_SHIFT 12
+
+struct MatH {
+  uint16_t* hi;  // fp16 or bf16 bits, row-major N x N per spin, spin stride N*N
+  uint16_t* lo;
+};
+
+struct sxl_ctx {
+  sxl_params p;
+  cudaStream_t st;
+  int nat, N, n2;
+  double beta;
+  std::string err;
+
+  // MD state and per-step vectors (device)
+  double *R, *V, *F, *nhist, *Kf, *q, *fres, *tmpv;
+  int hist_head;          // slot of n(t) in the nhist ring
+  double mu;
+  bool state_ready, evaluated, have_density, h0_valid;
+
+  // model data (device)
+  double *Rcur;           // positions of the current H0
+  double *gamma_m;        // N_at x N_at
+  double *H0;             // N x N
+  double *h0abs;          // N: sum_{j != i} |H0_ij|
+  double *shift;          // 2 x N_at per-atom diagonal shifts h_sigma
+  double *Fband;          // scratch force
+
+  // Fermi-operator-expansion chain (device); fp64 form uses the double
+  // buffers, mixed forms use the MatH ones.  Every matrix holds both spins.
+  int nr, nr_cap;
+  double scale;           // U = scale (H - mu I), scale = beta / 2^(nr+1)
+  double umax;            // bound on |eig(U)|
+  double lam_min, lam_max;
+  double *U, *S, *Q, *X0, *X1, *P, *Sm, *dTa, *dTb, *G1;
+  std::vector<double*> T, Y;
+  std::vector<int> ns_iters;  // Newton-Schulz iterations used at each step
+  // mixed-precision chain
+  MatH hU, hS, hQ, hX0, hX1, hP, hSm, hdTa, hdTb, hG1;
+  std::vector<MatH> hT, hY;
+
+  double *diagT, *rowsq, *chi;  // 2N each
+  double *du;                   // 2N perturbation (scaled) per orbital
+  double *dh;                   // 2 N_at
+  double *red;                  // reduction scratch (>= 4096 doubles)
+  double *hred;                 // pinned host scratch (64 doubles)
+
+  // Krylov
+  double *K0, *Vk, *FTk, *ftil, *cvec, *qv, *fv, *wvec, *Jm, *Jinv;
+  int *ipiv;
+
+  unsigned long long n_gemm;
+};
+
+// ---- error helpers ---------------------------------------------------------
+int sxl_fail(sxl_ctx* c, int code, const std::string& msg);
+#define CUDA_TRY(c, call)                                                     \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess)                                                    \
+      return sxl_fail((c), SXL_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+#define SXL_TRY(expr)                 \
+  do {                                \
+    int r_ = (expr);                  \
+    if (r_ != SXL_OK) return r_;      \
+  } while (0)
+
+// ---- model (model.cu) ------------------------------------------------------
+struct ModelConst {
+  double cell[3];
+  double eps[3];
+  double V0[10];
+  double q_decay, r0, r_cut, r_on;
+  double U, W, ck;
+  double rep_A, rep_b;
+};
+ModelConst model_const(const sxl_params& p);
+// H0 (N x N) from positions; also h0abs.
+void launch_build_h0(sxl_ctx* c, const double* R);
+// gamma (N_at x N_at) from positions
+void launch_build_gamma(sxl_ctx* c, const double* R);
+// per-atom shifts for the extended vector n (or a direction v, with
+// with_onsite = false it is the same linear map): out[sigma][I]
+void launch_spin_shift(sxl_ctx* c, const double* n, double* out);
+// forces at constant n from the density chain; erep_out: per-atom 1/2 Phi sums
+// Tsum_f64 / Tsum_h: T_up + T_dn source (one of them non-null)
+void launch_forces(sxl_ctx* c, const double* R, const double* n, const double* qspin,
+                   double* F, double* erep_atom);
+
+// ---- linear algebra (linalg.cu) ---------------------------------------------
+// C[b] = alpha A[b] B[b]^T + beta E[b] + gamma I over `batch` square n x n
+// matrices (batch stride n*n).  sym: C is known to be symmetric; only the
+// upper tiles are computed and mirrored (E must then be symmetric too).
+void gemm_f64(sxl_ctx* c, int batch, int n, const double* A, const double* B, double* C,
+              double alpha, const double* E, double beta, double gamma, bool sym);
+// out = a X + b (Y + Y^T) + cc (w_i + w_j) Z  (any of X, Y, Z, w may be null)
+void symcombo_f64(sxl_ctx* c, int batch, int n, double* out, double a, const double* X,
+                  double b, const double* Y, double cc, const double* w, const double* Z);
+void axpy_diag_f64(sxl_ctx* c, int batch, int n, double* out, double a, const double* X,
+                   double g);
+void build_u_f64(sxl_ctx* c, const double* H0, const double* shift, double mu, double scale,
+                 double* U);
+void rowstats_f64(sxl_ctx* c, int batch, int n, const double* T, double* diag, double* rowsq);
+void gersh_bounds(sxl_ctx* c, double* out2_dev);
+// deterministic dot products: out[0] = sum x.y (length len)
+void dot_f64(sxl_ctx* c, long long len, const double* x, const double* y, double* out);
+void small_kernels_density(sxl_ctx* c, double* q, double* stats);
+void small_kernels_response(sxl_ctx* c, double* qv, double* dmu);
+void perturb_du(sxl_ctx* c, const double* dh, double* du);
+void gemv_f64(sxl_ctx* c, int n, const double* A, const double* x, double* y, double a,
+              const double* z, double b);
+void krylov_orth(sxl_ctx* c, int k, const double* w, double* status);
+void krylov_lsq(sxl_ctx* c, int k, double* out_stats);
+void vec_axpby(sxl_ctx* c, int n, double* out, double a, const double* x, double b,
+               const double* y);
+void rms_f64(sxl_ctx* c, int n, const double* x, const double* y, double* out);
+int gauss_jordan_inverse(sxl_ctx* c, int n, double* A, double* Ainv);
+void md_half_kick(sxl_ctx* c, double* V, const double* F);
+void md_drift(sxl_ctx* c, double* R, const double* V);
+void md_nupdate(sxl_ctx* c, int head_new);
+void md_kinetic(sxl_ctx* c, const double* V, double* out);
+void energy_terms(sxl_ctx* c, const double* n, const double* erep_atom, double* out);
+
+// ---- mixed-precision chain (mixed.cu) ----------------------------------------
+int sxl_mixed_supported(sxl_ctx* c);
+void sxl_mixed_free(sxl_ctx* c);

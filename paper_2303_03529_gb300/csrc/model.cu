@@ -1,0 +1,360 @@
+// Model kernels: Slater-Koster H0 (image-summed), screened Coulomb gamma,
+// spin-resolved diagonal shifts, and the forces at constant n (Sec. III.A,
+// Eqs. ELatte, ShadowELatte, EqMot).
+//
+// The two-center element E_ab(d) of orbitals a at the origin and b at d is
+// evaluated by sk_elem<T>.  T = double gives the value (Hamiltonian build);
+// T = Dual3 carries the gradient with respect to the three components of d
+// (forces), so no derivative formula is written by hand.
+#include "common.cuh"
+
+// ---------------------------------------------------------------------------
+// forward-mode dual number with a 3-component gradient
+struct Dual3 {
+  double v, g0, g1, g2;
+  __device__ Dual3() {}
+  __device__ Dual3(double x) : v(x), g0(0), g1(0), g2(0) {}
+  __device__ Dual3(double x, double a, double b, double c) : v(x), g0(a), g1(b), g2(c) {}
+};
+__device__ inline Dual3 operator+(Dual3 a, Dual3 b) { return Dual3(a.v + b.v, a.g0 + b.g0, a.g1 + b.g1, a.g2 + b.g2); }
+__device__ inline Dual3 operator-(Dual3 a, Dual3 b) { return Dual3(a.v - b.v, a.g0 - b.g0, a.g1 - b.g1, a.g2 - b.g2); }
+__device__ inline Dual3 operator-(Dual3 a) { return Dual3(-a.v, -a.g0, -a.g1, -a.g2); }
+__device__ inline Dual3 operator*(Dual3 a, Dual3 b) {
+  return Dual3(a.v * b.v, a.g0 * b.v + a.v * b.g0, a.g1 * b.v + a.v * b.g1, a.g2 * b.v + a.v * b.g2);
+}
+__device__ inline Dual3 operator*(double s, Dual3 a) { return Dual3(s * a.v, s * a.g0, s * a.g1, s * a.g2); }
+__device__ inline Dual3 operator*(Dual3 a, double s) { return s * a; }
+__device__ inline Dual3 operator+(double s, Dual3 a) { return Dual3(s + a.v, a.g0, a.g1, a.g2); }
+__device__ inline Dual3 operator+(Dual3 a, double s) { return s + a; }
+__device__ inline Dual3 operator-(double s, Dual3 a) { return Dual3(s - a.v, -a.g0, -a.g1, -a.g2); }
+__device__ inline Dual3 operator-(Dual3 a, double s) { return Dual3(a.v - s, a.g0, a.g1, a.g2); }
+__device__ inline Dual3 operator/(Dual3 a, Dual3 b) {
+  double iv = 1.0 / b.v;
+  double q = a.v * iv;
+  return Dual3(q, (a.g0 - q * b.g0) * iv, (a.g1 - q * b.g1) * iv, (a.g2 - q * b.g2) * iv);
+}
+__device__ inline Dual3 dsqrt(Dual3 a) {
+  double s = sqrt(a.v);
+  double h = 0.5 / s;
+  return Dual3(s, a.g0 * h, a.g1 * h, a.g2 * h);
+}
+__device__ inline Dual3 dexp(Dual3 a) {
+  double e = exp(a.v);
+  return Dual3(e, a.g0 * e, a.g1 * e, a.g2 * e);
+}
+__device__ inline double dsqrt(double a) { return sqrt(a); }
+__device__ inline double dexp(double a) { return exp(a); }
+__device__ inline double val(double a) { return a; }
+__device__ inline double val(const Dual3& a) { return a.v; }
+
+ModelConst model_const(const sxl_params& p) {
+  ModelConst m;
+  for (int i = 0; i < 3; ++i) m.cell[i] = p.cell[i];
+  m.eps[0] = p.eps_s; m.eps[1] = p.eps_p; m.eps[2] = p.eps_d;
+  for (int i = 0; i < 10; ++i) m.V0[i] = p.V0[i];
+  m.q_decay = p.q_decay; m.r0 = p.r0; m.r_cut = p.r_cut; m.r_on = p.r_on;
+  m.U = p.U; m.W = p.W; m.ck = p.coulomb_k;
+  m.rep_A = p.rep_A; m.rep_b = p.rep_b;
+  return m;
+}
+
+__device__ __constant__ int c_ell[9] = {0, 1, 1, 1, 2, 2, 2, 2, 2};
+
+// C2 quintic switch: 1 below r_on, 0 above r_cut.
+template <class T>
+__device__ inline T switch_fn(T r, const ModelConst& m) {
+  double rv = val(r);
+  if (rv <= m.r_on) return T(1.0);
+  if (rv >= m.r_cut) return T(0.0);
+  T x = (r - m.r_on) * (1.0 / (m.r_cut - m.r_on));
+  T x3 = x * x * x;
+  return 1.0 - x3 * (10.0 - x * (15.0 - 6.0 * x));
+}
+
+// Slater-Koster two-center element for a <= b (orbital order s, px, py, pz,
+// dxy, dyz, dzx, dx2-y2, d3z2-r2); V = the ten bond integrals at |d|.
+// key = b for a = 0, else 10 a + (b - a): s-*: 0..8, x-*: 10..17, y-*: 20..26,
+// z-*: 30..35, xy-*: 40..44, yz-*: 50..53, zx-*: 60..62, x2-*: 70..71, z2: 80.
+template <class T>
+__device__ T sk_upper(int key, const T& l, const T& m, const T& n, const T* V) {
+  const double s3 = 1.7320508075688772;
+  const T &sss = V[0], &sps = V[1], &sds = V[2], &pps = V[3], &ppp = V[4];
+  const T &pds = V[5], &pdp = V[6], &dds = V[7], &ddp = V[8], &ddd = V[9];
+  T l2 = l * l, m2 = m * m, n2 = n * n;
+  T lm2 = l2 - m2;
+  T z2f = n2 - 0.5 * (l2 + m2);
+  switch (key) {
+    case 0:  return sss;                                     // s s
+    case 1:  return l * sps;                                 // s x
+    case 2:  return m * sps;                                 // s y
+    case 3:  return n * sps;                                 // s z
+    case 4:  return s3 * (l * m * sds);                      // s xy
+    case 5:  return s3 * (m * n * sds);                      // s yz
+    case 6:  return s3 * (n * l * sds);                      // s zx
+    case 7:  return (0.5 * s3) * (lm2 * sds);                // s x2
+    case 8:  return z2f * sds;                               // s z2
+    case 10: return l2 * pps + (1.0 - l2) * ppp;             // x x
+    case 11: return l * m * (pps - ppp);                     // x y
+    case 12: return l * n * (pps - ppp);                     // x z
+    case 13: return s3 * (l2 * m * pds) + m * (1.0 - 2.0 * l2) * pdp;        // x xy
+    case 14: return s3 * (l * m * n * pds) - 2.0 * (l * m * n * pdp);        // x yz
+    case 15: return s3 * (l2 * n * pds) + n * (1.0 - 2.0 * l2) * pdp;        // x zx
+    case 16: return (0.5 * s3) * (l * lm2 * pds) + l * (1.0 - lm2) * pdp;    // x x2
+    case 17: return l * z2f * pds - s3 * (l * n2 * pdp);                     // x z2
+    case 20: return m2 * pps + (1.0 - m2) * ppp;             // y y
+    case 21: return m * n * (pps - ppp);                     // y z
+    case 22: return s3 * (m2 * l * pds) + l * (1.0 - 2.0 * m2) * pdp;        // y xy
+    case 23: return s3 * (m2 * n * pds) + n * (1.0 - 2.0 * m2) * pdp;        // y yz
+    case 24: return s3 * (l * m * n * pds) - 2.0 * (l * m * n * pdp);        // y zx
+    case 25: return (0.5 * s3) * (m * lm2 * pds) - m * (1.0 + lm2) * pdp;    // y x2
+    case 26: return m * z2f * pds - s3 * (m * n2 * pdp);                     // y z2
+    case 30: return n2 * pps + (1.0 - n2) * ppp;             // z z
+    case 31: return s3 * (l * m * n * pds) - 2.0 * (l * m * n * pdp);        // z xy
+    case 32: return s3 * (n2 * m * pds) + m * (1.0 - 2.0 * n2) * pdp;        // z yz
+    case 33: return s3 * (n2 * l * pds) + l * (1.0 - 2.0 * n2) * pdp;        // z zx
+    case 34: return (0.5 * s3) * (n * lm2 * pds) - n * lm2 * pdp;            // z x2
+    case 35: return n * z2f * pds + s3 * (n * (l2 + m2) * pdp);              // z z2
+    case 40: return 3.0 * (l2 * m2 * dds) + (l2 + m2 - 4.0 * l2 * m2) * ddp + (n2 + l2 * m2) * ddd;
+    case 41: return 3.0 * (l * m2 * n * dds) + l * n * (1.0 - 4.0 * m2) * ddp + l * n * (m2 - 1.0) * ddd;
+    case 42: return 3.0 * (l2 * m * n * dds) + m * n * (1.0 - 4.0 * l2) * ddp + m * n * (l2 - 1.0) * ddd;
+    case 43: return 1.5 * (l * m * lm2 * dds) - 2.0 * (l * m * lm2 * ddp) + 0.5 * (l * m * lm2 * ddd);
+    case 44: return s3 * (l * m * z2f * dds) - (2.0 * s3) * (l * m * n2 * ddp) + (0.5 * s3) * (l * m * (1.0 + n2) * ddd);
+    case 50: return 3.0 * (m2 * n2 * dds) + (m2 + n2 - 4.0 * m2 * n2) * ddp + (l2 + m2 * n2) * ddd;
+    case 51: return 3.0 * (l * m * n2 * dds) + l * m * (1.0 - 4.0 * n2) * ddp + l * m * (n2 - 1.0) * ddd;
+    case 52: return 1.5 * (m * n * lm2 * dds) - m * n * (1.0 + 2.0 * lm2) * ddp + m * n * (1.0 + 0.5 * lm2) * ddd;
+    case 53: return s3 * (m * n * z2f * dds) + s3 * (m * n * (l2 + m2 - n2) * ddp) - (0.5 * s3) * (m * n * (l2 + m2) * ddd);
+    case 60: return 3.0 * (n2 * l2 * dds) + (n2 + l2 - 4.0 * n2 * l2) * ddp + (m2 + n2 * l2) * ddd;
+    case 61: return 1.5 * (n * l * lm2 * dds) + n * l * (1.0 - 2.0 * lm2) * ddp - n * l * (1.0 - 0.5 * lm2) * ddd;
+    case 62: return s3 * (l * n * z2f * dds) + s3 * (l * n * (l2 + m2 - n2) * ddp) - (0.5 * s3) * (l * n * (l2 + m2) * ddd);
+    case 70: return 0.75 * (lm2 * lm2 * dds) + (l2 + m2 - lm2 * lm2) * ddp + (n2 + 0.25 * (lm2 * lm2)) * ddd;
+    case 71: return (0.5 * s3) * (lm2 * z2f * dds) + s3 * (n2 * (m2 - l2) * ddp) + (0.25 * s3) * ((1.0 + n2) * lm2 * ddd);
+    case 80: return z2f * z2f * dds + 3.0 * (n2 * (l2 + m2) * ddp) + 0.75 * ((l2 + m2) * (l2 + m2) * ddd);
+    default: return T(0.0);
+  }
+}
+
+// general (a, b): lower entries by E_ba(d) = (-1)^(l_a + l_b) E_ab(d)
+template <class T>
+__device__ inline T sk_elem(int a, int b, const T& l, const T& m, const T& n, const T* V) {
+  if (a <= b) return sk_upper<T>(a == 0 ? b : 10 * a + (b - a), l, m, n, V);
+  T v = sk_elem<T>(b, a, l, m, n, V);
+  return ((c_ell[a] + c_ell[b]) & 1) ? -v : v;
+}
+
+// Bond integrals at distance r and the direction cosines of d.
+template <class T>
+__device__ inline void bond_setup(const T& dx, const T& dy, const T& dz, const ModelConst& mc,
+                                  T& l, T& m, T& n, T* V, T& r) {
+  r = dsqrt(dx * dx + dy * dy + dz * dz);
+  T ir = T(1.0) / r;
+  l = dx * ir; m = dy * ir; n = dz * ir;
+  T rad = dexp(-mc.q_decay * (r - mc.r0)) * switch_fn<T>(r, mc);
+#pragma unroll
+  for (int b = 0; b < 10; ++b) V[b] = mc.V0[b] * rad;
+}
+
+__device__ inline double min_image(double d, double L) { return d - L * rint(d / L); }
+
+// ---------------------------------------------------------------------------
+// H0: block (K) writes the 9 rows of atom K; each thread owns columns j.
+// For each column (atom J, orbital b) it sums E_ab over the 27 image shifts
+// of the minimum-image displacement with 0 < r < r_cut (fixed order, so the
+// sum is deterministic), for a = 0..8.
+__global__ void k_build_h0(int nat, const double* __restrict__ R, ModelConst mc,
+                           double* __restrict__ H0) {
+  const int K = blockIdx.x;
+  const int N = nat * NORB;
+  const double Kx = R[3 * K], Ky = R[3 * K + 1], Kz = R[3 * K + 2];
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const int J = j / NORB, b = j % NORB;
+    double acc[NORB];
+#pragma unroll
+    for (int a = 0; a < NORB; ++a) acc[a] = 0.0;
+    double dx0 = min_image(R[3 * J] - Kx, mc.cell[0]);
+    double dy0 = min_image(R[3 * J + 1] - Ky, mc.cell[1]);
+    double dz0 = min_image(R[3 * J + 2] - Kz, mc.cell[2]);
+    for (int s = 0; s < 27; ++s) {
+      double dx = dx0 + (s / 9 - 1) * mc.cell[0];
+      double dy = dy0 + ((s / 3) % 3 - 1) * mc.cell[1];
+      double dz = dz0 + (s % 3 - 1) * mc.cell[2];
+      double r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 >= mc.r_cut * mc.r_cut || r2 < 1e-16) continue;
+      double l, m, n, r, V[10];
+      bond_setup<double>(dx, dy, dz, mc, l, m, n, V, r);
+#pragma unroll
+      for (int a = 0; a < NORB; ++a) acc[a] += sk_elem<double>(a, b, l, m, n, V);
+    }
+    if (J == K) acc[b] += mc.eps[c_ell[b]];
+#pragma unroll
+    for (int a = 0; a < NORB; ++a) H0[(size_t)(NORB * K + a) * N + j] = acc[a];
+  }
+}
+
+// h0abs[i] = sum_{j != i} |H0_ij| (Gershgorin radii), one warp per row.
+__global__ void k_rowabs(int N, const double* __restrict__ H0, double* __restrict__ out) {
+  int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  int lane = threadIdx.x & 31;
+  if (row >= N) return;
+  double s = 0.0;
+  for (int j = lane; j < N; j += 32)
+    if (j != row) s += fabs(H0[(size_t)row * N + j]);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) out[row] = s;
+}
+
+void launch_build_h0(sxl_ctx* c, const double* R) {
+  ModelConst mc = model_const(c->p);
+  LAUNCH(k_build_h0, c->nat, 256, 0, c->st, c->nat, R, mc, c->H0);
+  int wpb = 8;
+  LAUNCH(k_rowabs, (c->N + wpb - 1) / wpb, 32 * wpb, 0, c->st, c->N, c->H0, c->h0abs);
+}
+
+// gamma_IJ = k / sqrt(r^2 + (k/U)^2), minimum image, gamma_II = U
+__global__ void k_build_gamma(int nat, const double* __restrict__ R, ModelConst mc,
+                              double* __restrict__ G) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nat * nat) return;
+  int I = idx / nat, J = idx % nat;
+  if (I == J) { G[idx] = mc.U; return; }
+  double dx = min_image(R[3 * J] - R[3 * I], mc.cell[0]);
+  double dy = min_image(R[3 * J + 1] - R[3 * I + 1], mc.cell[1]);
+  double dz = min_image(R[3 * J + 2] - R[3 * I + 2], mc.cell[2]);
+  double a = mc.ck / mc.U;
+  G[idx] = mc.ck / sqrt(dx * dx + dy * dy + dz * dz + a * a);
+}
+
+void launch_build_gamma(sxl_ctx* c, const double* R) {
+  int n = c->nat * c->nat;
+  LAUNCH(k_build_gamma, (n + 255) / 256, 256, 0, c->st, c->nat, R, model_const(c->p), c->gamma_m);
+}
+
+// out[sigma*nat + I] = (gamma (n_up + n_dn))_I + sigma (W/2) (n_up - n_dn)_I
+// (sigma = +1 for the first block, -1 for the second); one warp per atom.
+__global__ void k_spin_shift(int nat, const double* __restrict__ G, const double* __restrict__ n,
+                             double W, double* __restrict__ out) {
+  int I = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  int lane = threadIdx.x & 31;
+  if (I >= nat) return;
+  double s = 0.0;
+  for (int J = lane; J < nat; J += 32) s += G[(size_t)I * nat + J] * (n[J] + n[nat + J]);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    double sp = n[I] - n[nat + I];
+    out[I] = s + 0.5 * W * sp;
+    out[nat + I] = s - 0.5 * W * sp;
+  }
+}
+
+void launch_spin_shift(sxl_ctx* c, const double* n, double* out) {
+  int wpb = 8;
+  LAUNCH(k_spin_shift, (c->nat + wpb - 1) / wpb, 32 * wpb, 0, c->st, c->nat, c->gamma_m, n,
+         c->p.W, out);
+}
+
+// ---------------------------------------------------------------------------
+// Forces at constant n.  Block per atom K, warps over partner atoms J:
+//   band:  F_K += 2 sum_{J != K, images} sum_ab Dsum_{Ka,Jb} dE_ab/dd
+//          with Dsum = D_up + D_dn = -(T_up + T_dn)/2 off the diagonal blocks,
+//   repulsion: F_K += sum_images dPhi(|d|)/dd, E_rep,K = 1/2 sum Phi,
+// then the Coulomb term of E_coul = 1/2 sum (2q - n)_I gamma_IJ n_J:
+//   F_K += 1/2 sum_J (R_K - R_J) gamma_KJ^3 / k^2 (a_J b_K + a_K b_J),
+//   a = 2q - n, b = n (per-atom totals).
+// The sums run in a fixed order, so the result is deterministic.
+template <class TS>
+__device__ inline double tsum_at(const TS& ts, size_t idx);
+
+struct TsumF64 {
+  const double* T;   // 2 x N x N
+  size_t nn;
+};
+template <>
+__device__ inline double tsum_at<TsumF64>(const TsumF64& ts, size_t idx) {
+  return ts.T[idx] + ts.T[ts.nn + idx];
+}
+
+template <class TS>
+__global__ void __launch_bounds__(256) k_forces(int nat, const double* __restrict__ R,
+                                                ModelConst mc, TS ts,
+                                                const double* __restrict__ n,
+                                                const double* __restrict__ qspin,
+                                                double* __restrict__ F,
+                                                double* __restrict__ erep) {
+  const int K = blockIdx.x;
+  const int N = nat * NORB;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  double fx = 0.0, fy = 0.0, fz = 0.0, er = 0.0;
+  const double Kx = R[3 * K], Ky = R[3 * K + 1], Kz = R[3 * K + 2];
+  for (int J = warp; J < nat; J += nwarps) {
+    if (J == K) continue;  // self-image bonds do not depend on R_K
+    double dx0 = min_image(R[3 * J] - Kx, mc.cell[0]);
+    double dy0 = min_image(R[3 * J + 1] - Ky, mc.cell[1]);
+    double dz0 = min_image(R[3 * J + 2] - Kz, mc.cell[2]);
+    bool in = false;
+    if (lane < 27) {
+      double dx = dx0 + (lane / 9 - 1) * mc.cell[0];
+      double dy = dy0 + ((lane / 3) % 3 - 1) * mc.cell[1];
+      double dz = dz0 + (lane % 3 - 1) * mc.cell[2];
+      in = dx * dx + dy * dy + dz * dz < mc.r_cut * mc.r_cut;
+    }
+    unsigned mask = __ballot_sync(0xffffffffu, in);
+    while (mask) {
+      int s = __ffs(mask) - 1;
+      mask &= mask - 1;
+      Dual3 dx(dx0 + (s / 9 - 1) * mc.cell[0], 1.0, 0.0, 0.0);
+      Dual3 dy(dy0 + ((s / 3) % 3 - 1) * mc.cell[1], 0.0, 1.0, 0.0);
+      Dual3 dz(dz0 + (s % 3 - 1) * mc.cell[2], 0.0, 0.0, 1.0);
+      Dual3 l, m, nn, V[10], r;
+      bond_setup<Dual3>(dx, dy, dz, mc, l, m, nn, V, r);
+      for (int e = lane; e < NORB * NORB; e += 32) {
+        int a = e / NORB, b = e % NORB;
+        Dual3 E = sk_elem<Dual3>(a, b, l, m, nn, V);
+        double dsum = -0.5 * tsum_at<TS>(ts, (size_t)(NORB * K + a) * N + NORB * J + b);
+        fx += 2.0 * dsum * E.g0;
+        fy += 2.0 * dsum * E.g1;
+        fz += 2.0 * dsum * E.g2;
+      }
+      if (lane == 0 && mc.rep_A != 0.0) {
+        Dual3 phi = mc.rep_A * dexp(-mc.rep_b * (r - mc.r0)) * switch_fn<Dual3>(r, mc);
+        fx += phi.g0; fy += phi.g1; fz += phi.g2;
+        er += 0.5 * phi.v;
+      }
+    }
+  }
+  // Coulomb term (threads over J)
+  const double a_K = 2.0 * (qspin[K] + qspin[nat + K]) - (n[K] + n[nat + K]);
+  const double b_K = n[K] + n[nat + K];
+  const double ak2 = (mc.ck / mc.U) * (mc.ck / mc.U);
+  for (int J = threadIdx.x; J < nat; J += blockDim.x) {
+    if (J == K) continue;
+    double dx = min_image(R[3 * J] - Kx, mc.cell[0]);
+    double dy = min_image(R[3 * J + 1] - Ky, mc.cell[1]);
+    double dz = min_image(R[3 * J + 2] - Kz, mc.cell[2]);
+    double g = mc.ck / sqrt(dx * dx + dy * dy + dz * dz + ak2);
+    double a_J = 2.0 * (qspin[J] + qspin[nat + J]) - (n[J] + n[nat + J]);
+    double b_J = n[J] + n[nat + J];
+    double w = 0.5 * g * g * g / (mc.ck * mc.ck) * (a_J * b_K + a_K * b_J);
+    fx -= w * dx; fy -= w * dy; fz -= w * dz;
+  }
+  // block reduction in a fixed order
+  __shared__ double red[4][256];
+  red[0][threadIdx.x] = fx; red[1][threadIdx.x] = fy; red[2][threadIdx.x] = fz;
+  red[3][threadIdx.x] = er;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int k = 0; k < 4; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    F[3 * K] = red[0][0]; F[3 * K + 1] = red[1][0]; F[3 * K + 2] = red[2][0];
+    erep[K] = red[3][0];
+  }
+}
+
+void launch_forces(sxl_ctx* c, const double* R, const double* n, const double* qspin,
+                   double* F, double* erep_atom) {
+  ModelConst mc = model_const(c->p);
+  TsumF64 ts{c->T[c->nr], (size_t)c->N * c->N};
+  LAUNCH(k_forces<TsumF64>, c->nat, 256, 0, c->st, c->nat, R, mc, ts, n, qspin, F, erep_atom);
+}

@@ -1,0 +1,295 @@
+"""Python binding of libsxl.so (include/sxl.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels; this module only
+checks shapes, passes device pointers of torch tensors and the stream, and
+turns status codes into exceptions.  Importing it does not need a GPU;
+creating a Context does, and fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsxl.so")
+
+FP64, MIXED_FP16, MIXED_BF16 = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "fp16": MIXED_FP16, "bf16": MIXED_BF16}
+K0_MINUS_IDENTITY, K0_GIVEN = 0, 1
+
+_d = ctypes.c_double
+_i = ctypes.c_int
+_p = ctypes.c_void_p
+
+
+class Params(ctypes.Structure):
+    """Mirror of sxl_params (include/sxl.h)."""
+    _fields_ = [
+        ("n_atoms", _i), ("cell", _d * 3),
+        ("eps_s", _d), ("eps_p", _d), ("eps_d", _d),
+        ("V0", _d * 10),
+        ("q_decay", _d), ("r0", _d), ("r_cut", _d), ("r_on", _d),
+        ("U", _d), ("W", _d), ("coulomb_k", _d),
+        ("kT", _d), ("n_elec_per_atom", _d),
+        ("d0_s", _d), ("d0_p", _d), ("d0_d", _d),
+        ("rep_A", _d), ("rep_b", _d),
+        ("mass_amu", _d), ("dt_fs", _d),
+        ("krylov_rank", _i), ("kmax", _i),
+        ("kappa", _d), ("alpha", _d), ("c", _d * 10),
+        ("precision", _i), ("foe_steps", _i), ("foe_u_max", _d),
+        ("mu_max_iter", _i), ("mu_tol", _d),
+    ]
+
+
+EXPORTS = {
+    "sxl_create": (_i, [ctypes.POINTER(Params), _p, ctypes.POINTER(_p)]),
+    "sxl_destroy": (_i, [_p]),
+    "sxl_last_error": (ctypes.c_char_p, [_p]),
+    "sxl_hamiltonian": (_i, [_p, _p, _p, _p]),
+    "sxl_density": (_i, [_p, _p, _p, _p, ctypes.POINTER(_d)]),
+    "sxl_density_matrix": (_i, [_p, _p]),
+    "sxl_response": (_i, [_p, _p, _p, ctypes.POINTER(_d)]),
+    "sxl_set_k0": (_i, [_p, _i, _p]),
+    "sxl_build_exact_k0": (_i, [_p, _p]),
+    "krylov_kernel_apply": (_i, [_p, _p, _p, _i, _p, _p, ctypes.POINTER(_d)]),
+    "forces": (_i, [_p, _p, _p, _p, _p]),
+    "sxl_set_state": (_i, [_p, _p, _p, _p, _d]),
+    "sxl_get_state": (_i, [_p, _p, _p, _p, ctypes.POINTER(_d)]),
+    "sxl_set_state_host": (_i, [_p, _p, _p, _p, _d]),
+    "sxl_get_state_host": (_i, [_p, _p, _p, _p, ctypes.POINTER(_d)]),
+    "xlbomd_step": (_i, [_p, _i, _p]),
+    "scf_solve": (_i, [_p, _p, _p, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
+    "sxl_info": (_i, [_p, _p]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libsxl.so and declares the C signatures; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsxl.so not found at {path}: run __graft_entry__.build() first")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class SxlError(RuntimeError):
+    pass
+
+
+def make_params(mp, n_atoms: int, cell, precision="fp64", foe_steps=0, foe_u_max=0.0,
+                mu_tol=0.0, mu_max_iter=0) -> Params:
+    """Params from a workload.ModelParams-like object."""
+    p = Params()
+    p.n_atoms = int(n_atoms)
+    p.cell[:] = [float(x) for x in cell]
+    p.eps_s, p.eps_p, p.eps_d = mp.eps_s, mp.eps_p, mp.eps_d
+    p.V0[:] = [float(x) for x in mp.V0]
+    p.q_decay, p.r0, p.r_cut, p.r_on = mp.q_decay, mp.r0, mp.r_cut, mp.r_on
+    p.U, p.W, p.coulomb_k = mp.U, mp.W, mp.coulomb_k
+    p.kT, p.n_elec_per_atom = mp.kT, mp.n_elec_per_atom
+    p.d0_s, p.d0_p, p.d0_d = mp.d0_s, mp.d0_p, mp.d0_d
+    p.rep_A, p.rep_b = mp.rep_A, mp.rep_b
+    p.mass_amu, p.dt_fs = mp.mass_amu, mp.dt_fs
+    p.krylov_rank, p.kmax = int(mp.krylov_rank), int(mp.kmax)
+    p.kappa, p.alpha = mp.kappa, mp.alpha
+    cc = list(mp.c) + [0.0] * (10 - len(mp.c))
+    p.c[:] = [float(x) for x in cc]
+    p.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    p.foe_steps = int(foe_steps)
+    p.foe_u_max = float(foe_u_max)
+    p.mu_max_iter = int(mu_max_iter)
+    p.mu_tol = float(mu_tol)
+    return p
+
+
+def _ptr(t, n=None, name="array"):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
+        raise TypeError(f"{name} must be a float64 CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} must have {n} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One library context (device buffers, stream, MD state)."""
+
+    def __init__(self, mp, n_atoms: int, cell, precision="fp64", stream=None, **kw):
+        import torch
+        self.lib = load_library()
+        self.nat = int(n_atoms)
+        self.N = 9 * self.nat
+        self.n2 = 2 * self.nat
+        self.kmax = int(mp.kmax)
+        self.params = make_params(mp, n_atoms, cell, precision, **kw)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = _p()
+        rc = self.lib.sxl_create(ctypes.byref(self.params), _p(self.stream.cuda_stream),
+                                 ctypes.byref(h))
+        if rc != 0:
+            raise SxlError(f"sxl_create failed with code {rc}")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sxl_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != 0:
+            msg = self.lib.sxl_last_error(self.h).decode()
+            raise SxlError(f"{what} failed ({rc}): {msg}")
+
+    def _dev(self, x):
+        import torch
+        if isinstance(x, torch.Tensor):
+            return x.to(device="cuda", dtype=torch.float64).contiguous()
+        return torch.as_tensor(np.asarray(x, dtype=np.float64), device="cuda").contiguous()
+
+    def _new(self, *shape):
+        import torch
+        return torch.empty(*shape, dtype=torch.float64, device="cuda")
+
+    # -- stages -------------------------------------------------------------
+    def hamiltonian(self, R, n, want_H=True):
+        R, n = self._dev(R), self._dev(n)
+        H = self._new(2, self.N, self.N) if want_H else None
+        self._check(self.lib.sxl_hamiltonian(self.h, _ptr(R, 3 * self.nat), _ptr(n, self.n2),
+                                             _ptr(H)), "sxl_hamiltonian")
+        return H
+
+    def density(self, R, n, mu: Optional[float] = None):
+        R, n = self._dev(R), self._dev(n)
+        q = self._new(self.n2)
+        m = _d(float("nan") if mu is None else float(mu))
+        self._check(self.lib.sxl_density(self.h, _ptr(R, 3 * self.nat), _ptr(n, self.n2),
+                                         _ptr(q), ctypes.byref(m)), "sxl_density")
+        return q, m.value
+
+    def density_matrix(self):
+        D = self._new(2, self.N, self.N)
+        self._check(self.lib.sxl_density_matrix(self.h, _ptr(D)), "sxl_density_matrix")
+        return D
+
+    def response(self, v):
+        v = self._dev(v)
+        qv = self._new(self.n2)
+        dmu = _d(0.0)
+        self._check(self.lib.sxl_response(self.h, _ptr(v, self.n2), _ptr(qv), ctypes.byref(dmu)),
+                    "sxl_response")
+        return qv, dmu.value
+
+    def set_k0(self, K0=None):
+        if K0 is None:
+            self._check(self.lib.sxl_set_k0(self.h, K0_MINUS_IDENTITY, None), "sxl_set_k0")
+        else:
+            K0 = self._dev(K0)
+            self._check(self.lib.sxl_set_k0(self.h, K0_GIVEN, _ptr(K0, self.n2 * self.n2)),
+                        "sxl_set_k0")
+
+    def build_exact_k0(self, want_J=False):
+        J = self._new(self.n2, self.n2) if want_J else None
+        self._check(self.lib.sxl_build_exact_k0(self.h, _ptr(J)), "sxl_build_exact_k0")
+        return J
+
+    def krylov(self, R, n, rank):
+        R, n = self._dev(R), self._dev(n)
+        Kf, q = self._new(self.n2), self._new(self.n2)
+        rel = _d(0.0)
+        self._check(self.lib.krylov_kernel_apply(self.h, _ptr(R, 3 * self.nat), _ptr(n, self.n2),
+                                                 int(rank), _ptr(Kf), _ptr(q), ctypes.byref(rel)),
+                    "krylov_kernel_apply")
+        return Kf, q, rel.value
+
+    def forces(self, R, n, energies=True):
+        R, n = self._dev(R), self._dev(n)
+        F = self._new(self.nat, 3)
+        en = (ctypes.c_double * 6)() if energies else None
+        self._check(self.lib.forces(self.h, _ptr(R, 3 * self.nat), _ptr(n, self.n2), _ptr(F),
+                                    en), "forces")
+        if not energies:
+            return F, None
+        keys = ("U", "band", "coul", "spin", "entropy", "rep")
+        return F, dict(zip(keys, list(en)))
+
+    # -- MD -----------------------------------------------------------------
+    def set_state(self, R, V, nhist, mu):
+        R, V, nh = self._dev(R), self._dev(V), self._dev(nhist)
+        self._check(self.lib.sxl_set_state(self.h, _ptr(R, 3 * self.nat), _ptr(V, 3 * self.nat),
+                                           _ptr(nh, (self.kmax + 1) * self.n2), float(mu)),
+                    "sxl_set_state")
+
+    def get_state(self):
+        R, V = self._new(self.nat, 3), self._new(self.nat, 3)
+        nh = self._new(self.kmax + 1, self.n2)
+        mu = _d(0.0)
+        self._check(self.lib.sxl_get_state(self.h, _ptr(R), _ptr(V), _ptr(nh), ctypes.byref(mu)),
+                    "sxl_get_state")
+        return R, V, nh, mu.value
+
+    def set_state_host(self, R, V, nhist, mu):
+        """Host-pointer variant: R, V, nhist are C-contiguous float64 numpy arrays
+        (pinned torch CPU tensors also work)."""
+        ptrs = [_host_ptr(a) for a in (R, V, nhist)]
+        self._check(self.lib.sxl_set_state_host(self.h, *ptrs, float(mu)), "sxl_set_state_host")
+
+    def get_state_host(self, R, V, nhist):
+        mu = _d(0.0)
+        ptrs = [_host_ptr(a) for a in (R, V, nhist)]
+        self._check(self.lib.sxl_get_state_host(self.h, *ptrs, ctypes.byref(mu)),
+                    "sxl_get_state_host")
+        return mu.value
+
+    def step(self, nsteps=1, stats=True):
+        out = np.zeros((max(nsteps, 1), 4)) if stats else None
+        ptr = out.ctypes.data_as(_p) if stats else None
+        self._check(self.lib.xlbomd_step(self.h, int(nsteps), ptr), "xlbomd_step")
+        return out
+
+    def scf(self, R, n, tol=1e-8, max_iter=300):
+        R = self._dev(R)
+        n = self._dev(n).clone()
+        it, rms = _i(0), _d(0.0)
+        self._check(self.lib.scf_solve(self.h, _ptr(R, 3 * self.nat), _ptr(n, self.n2),
+                                       float(tol), int(max_iter), ctypes.byref(it),
+                                       ctypes.byref(rms)), "scf_solve")
+        return n, it.value, rms.value
+
+    def info(self):
+        out = np.zeros(7)
+        self._check(self.lib.sxl_info(self.h, out.ctypes.data_as(_p)), "sxl_info")
+        keys = ("mu", "N", "foe_steps", "lam_min", "lam_max", "gemms", "launches")
+        return dict(zip(keys, out.tolist()))
+
+
+def _host_ptr(a):
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("host arrays must be contiguous float64 CPU tensors")
+        return _p(a.data_ptr())
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a.ctypes.data_as(_p)
