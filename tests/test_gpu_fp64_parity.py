@@ -110,3 +110,26 @@ def test_scf_fixed_point(lib):
     res = dynamics.scf(w.R, w.cell, w.n0, w.params, tol=1e-9)
     assert rms < 1e-9
     np.testing.assert_allclose(_np(n), res["n"], atol=1e-8)
+
+
+def test_xlbomd_trajectory_matches_oracle(lib):
+    """Ten sXL-BOMD steps from the SCF point (exact K0, rank 4): positions,
+    velocities, n, total energy without the entropy term and mu follow the
+    oracle step by step."""
+    w = wl.fe16()
+    res = dynamics.scf(w.R, w.cell, w.n0, w.params, tol=1e-10)
+    md = dynamics.XLBOMD(w.R, w.V, w.cell, res["n"], w.params, res["K0"], mu=res["mu"])
+    ctx = _ctx(lib, w)
+    ctx.set_k0(res["K0"])
+    nh = np.tile(res["n"], (w.params.kmax + 1, 1))
+    ctx.set_state(w.R, w.V, nh, res["mu"])
+    for step in range(10):
+        st_o = md.step()
+        st = ctx.step(1)[0]
+        R, V, nhg, mu = ctx.get_state()
+        np.testing.assert_allclose(_np(R), md.R, atol=1e-10)
+        np.testing.assert_allclose(_np(V), md.V, atol=1e-11)
+        np.testing.assert_allclose(_np(nhg)[0], md.nhist[0], atol=1e-9)
+        assert abs(mu - st_o["mu"]) < 1e-9
+        assert abs(st[1] - st_o["T"]) < 1e-6
+        assert abs(st[2] - st_o["rms"]) < 1e-9
