@@ -168,6 +168,16 @@ int xlbomd_step(sxl_ctx* ctx, int nsteps, double* stats_host);
 int scf_solve(sxl_ctx* ctx, const double* R_dev, double* n_dev, double tol,
               int max_iter, int* iters_out, double* rms_out);
 
+/* Diagnostic: C[b] = alpha A[b] B[b]^T + beta E[b] + gamma I (b = 0, 1; each
+ * N x N, row-major fp64 device arrays, E may be NULL) through the library's
+ * tensor-core GEMM, the product every step of the mixed-precision chains
+ * uses: inputs are rounded to (hi, lo) 16-bit pairs, split = 1 forms the
+ * three-product form, split = 0 the hi x hi product only; sym = 1 computes
+ * the upper tiles and mirrors them (valid only for a symmetric result).
+ * Needs a context created with SXL_MIXED_FP16 or SXL_MIXED_BF16. */
+int sxl_mixed_gemm(sxl_ctx* ctx, const double* A_dev, const double* B_dev, const double* E_dev,
+                   double* C_dev, double alpha, double beta, double gamma, int sym, int split);
+
 /* Diagnostics of the last density: [mu, N(mu), foe_steps, lambda_min,
  * lambda_max, GEMM launches so far, own kernel launches so far]. */
 int sxl_info(sxl_ctx* ctx, double* out7);

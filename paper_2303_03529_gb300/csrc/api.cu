@@ -176,9 +176,16 @@ static int density(sxl_ctx* c, const double* R, const double* n, double mu_guess
   const int maxit = c->p.mu_max_iter > 0 ? c->p.mu_max_iter : 30;
   const double tol = c->p.mu_tol > 0 ? c->p.mu_tol : 1e-10;
   double* stats = c->red + 16;
+  const bool mixed = c->p.precision != SXL_FP64;
   for (int it = 0;; ++it) {
-    SXL_TRY(foe_f64(c, mu, stats));
+    if (mixed) SXL_TRY(foe_mixed(c, mu, stats));
+    else SXL_TRY(foe_f64(c, mu, stats));
     SXL_TRY(sync_host(c, stats, 2));
+    if (mixed) {
+      int flag = 0;
+      SXL_TRY(tc_error_flag(c, &flag));
+      if (flag) return sxl_fail(c, SXL_E_CUDA, "tensor-core GEMM reported a wait timeout");
+    }
     double Nmu = c->hred[0], dN = c->hred[1];
     if (!std::isfinite(Nmu) || !std::isfinite(dN)) return sxl_fail(c, SXL_E_NAN, "non-finite density");
     double err = Nmu - Ne;
@@ -199,7 +206,8 @@ static int response(sxl_ctx* c, const double* v, double* qv, double* dmu_dev) {
   if (!c->have_density) return sxl_fail(c, SXL_E_STATE, "no density: call sxl_density first");
   launch_spin_shift(c, v, c->dh);
   perturb_du(c, c->dh, c->du);
-  SXL_TRY(dmpt_f64(c, c->du));
+  if (c->p.precision != SXL_FP64) SXL_TRY(dmpt_mixed(c, c->du));
+  else SXL_TRY(dmpt_f64(c, c->du));
   small_kernels_response(c, qv, dmu_dev);
   return SXL_OK;
 }
@@ -283,8 +291,13 @@ static int eval_forces(sxl_ctx* c, const double* R, const double* n, double* F, 
   if (en) {
     const size_t nn = (size_t)c->N * c->N;
     double* d = c->red + 64;
-    dot_f64(c, (long long)nn, c->H0, c->T[c->nr], d);
-    dot_f64(c, (long long)nn, c->H0, c->T[c->nr] + nn, d + 1);
+    if (c->p.precision != SXL_FP64) {
+      dot_h0_t_mixed(c, 0, d);
+      dot_h0_t_mixed(c, 1, d + 1);
+    } else {
+      dot_f64(c, (long long)nn, c->H0, c->T[c->nr], d);
+      dot_f64(c, (long long)nn, c->H0, c->T[c->nr] + nn, d + 1);
+    }
     LAUNCH(k_energy_band, 1, 1024, 0, c->st, c->N, c->H0, c->p.d0_s, c->p.d0_p, c->p.d0_d, d,
            d + 2);
     energy_terms(c, n, erep, d + 3);
@@ -341,8 +354,10 @@ int sxl_create(const sxl_params* prm, void* stream, sxl_ctx** out) {
   AL(R, 3 * nat); AL(V, 3 * nat); AL(F, 3 * nat); AL(Rcur, 3 * nat); AL(Fband, 3 * nat);
   AL(nhist, (size_t)K1 * n2); AL(Kf, n2); AL(q, n2); AL(fres, n2); AL(tmpv, std::max(n2, 3 * nat));
   AL(gamma_m, (size_t)nat * nat); AL(H0, (size_t)N * N); AL(h0abs, N); AL(shift, 2 * nat);
-  AL(U, mm); AL(S, mm); AL(Q, mm); AL(X0, mm); AL(X1, mm); AL(P, mm); AL(Sm, mm);
-  AL(dTa, mm); AL(dTb, mm); AL(G1, mm);
+  if (p.precision == SXL_FP64) {
+    AL(U, mm); AL(S, mm); AL(Q, mm); AL(X0, mm); AL(X1, mm); AL(P, mm); AL(Sm, mm);
+    AL(dTa, mm); AL(dTb, mm); AL(G1, mm);
+  }
   AL(diagT, 4 * N); AL(rowsq, 2 * N); AL(chi, 2 * N); AL(du, 2 * N); AL(dh, 2 * nat);
   AL(red, 4096);
   AL(K0, (size_t)n2 * n2); AL(Vk, (size_t)32 * n2); AL(FTk, (size_t)32 * n2); AL(ftil, n2);
@@ -410,7 +425,8 @@ int sxl_density_matrix(sxl_ctx* c, double* D) {
   if (!c || !D) return SXL_E_ARG;
   if (!c->have_density) return sxl_fail(c, SXL_E_STATE, "no density");
   size_t nn = 2 * (size_t)c->N * c->N;
-  LAUNCH(k_d_from_t, (unsigned)((nn + 255) / 256), 256, 0, c->st, nn, c->T[c->nr], D, c->N);
+  if (c->p.precision != SXL_FP64) density_matrix_mixed(c, D);
+  else LAUNCH(k_d_from_t, (unsigned)((nn + 255) / 256), 256, 0, c->st, nn, c->T[c->nr], D, c->N);
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   return SXL_OK;
 }
@@ -613,6 +629,18 @@ int scf_solve(sxl_ctx* c, const double* R, double* n, double tol, int max_iter, 
   if (rms_out) *rms_out = rms;
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   if (!(rms < tol)) return sxl_fail(c, SXL_E_NO_CONVERGENCE, "SCF hit max_iter");
+  return SXL_OK;
+}
+
+int sxl_mixed_gemm(sxl_ctx* c, const double* A, const double* B, const double* E, double* C,
+                   double alpha, double beta, double gamma, int sym, int split) {
+  if (!c || !A || !B || !C) return SXL_E_ARG;
+  if (c->p.precision == SXL_FP64) return sxl_fail(c, SXL_E_STATE, "context is fp64");
+  SXL_TRY(mixed_gemm_test(c, A, B, E, C, alpha, beta, gamma, sym, split));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  int flag = 0;
+  SXL_TRY(tc_error_flag(c, &flag));
+  if (flag) return sxl_fail(c, SXL_E_CUDA, "tensor-core GEMM reported a wait timeout");
   return SXL_OK;
 }
 

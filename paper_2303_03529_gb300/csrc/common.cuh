@@ -151,3 +151,20 @@ void energy_terms(sxl_ctx* c, const double* n, const double* erep_atom, double* 
 // ---- mixed-precision chain (mixed.cu) ----------------------------------------
 int sxl_mixed_supported(sxl_ctx* c);
 void sxl_mixed_free(sxl_ctx* c);
+int foe_mixed(sxl_ctx* c, double mu, double* stats_dev);
+int dmpt_mixed(sxl_ctx* c, const double* du);
+void dot_h0_t_mixed(sxl_ctx* c, int spin, double* out);
+void density_matrix_mixed(sxl_ctx* c, double* D);
+int tc_error_flag(sxl_ctx* c, int* flag);
+int mixed_gemm_test(sxl_ctx* c, const double* A, const double* B, const double* E, double* C,
+                    double alpha, double beta, double gamma, int sym, int split);
+
+// value of element i of a (hi, lo) matrix: hi + lo 2^-LO_SHIFT
+template <bool BF16>
+__device__ __forceinline__ double hl_value(const uint16_t* hi, const uint16_t* lo, size_t i) {
+  if (BF16)
+    return (double)__bfloat162float(__ushort_as_bfloat16(hi[i])) +
+           (double)__bfloat162float(__ushort_as_bfloat16(lo[i])) * (1.0 / 4096.0);
+  return (double)__half2float(__ushort_as_half(hi[i])) +
+         (double)__half2float(__ushort_as_half(lo[i])) * (1.0 / 4096.0);
+}

@@ -1,7 +1,755 @@
-// Mixed-precision (fp16 / bf16 tensor-core) expansion chain.
+// Mixed-precision form of the Fermi-operator expansion and its response:
+// every GEMM of the chains runs on the 5th-generation tensor cores
+// (tcgen05.mma kind::f16, fp16 or bf16 operands, fp32 accumulation in TMEM),
+// operands staged by TMA into 128B-swizzled shared memory.
+//
+// Each matrix is stored as a pair (hi, lo) of 16-bit tensors with
+// value = hi + lo 2^-12: hi = rn(x), lo = rn((x - hi) 2^12).  A product is
+// formed in one of two modes:
+//   plain:  acc0 = A_hi B_hi^T                           (1 MMA per k step)
+//   split:  acc0 = A_hi B_hi^T, acc1 = A_hi B_lo^T + A_lo B_hi^T
+//           C = acc0 + acc1 2^-12                        (3 MMAs per k step)
+// The split form carries the fp32 residual of each operand into the product
+// (about 22 significant bits with fp16, 16 with bf16), which the recursion
+// needs because rounding errors of early doubling steps are amplified up to
+// 2^nr near the chemical potential.
+//
+// Kernel layout (one CTA per 128 x 256 output tile, 192 threads):
+//   warp 0: TMA producer, warp 1: TMEM allocator + MMA issuer (one thread),
+//   warps 2-5: epilogue (TMEM -> registers -> alpha acc + beta E + gamma I ->
+//   hi/lo stores; symmetric outputs also store the mirrored element).
+// Every wait is bounded (2 s of %globaltimer); on a timeout the CTA records
+// an error, waits (bounded) for its in-flight copies and MMAs, frees TMEM and
+// returns.
 #include "common.cuh"
 
-int sxl_mixed_supported(sxl_ctx* c) {
-  return sxl_fail(c, SXL_E_UNSUPPORTED, "mixed precision not built");
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+
+#define TC_BM 128
+#define TC_BN 256
+#define TC_BK 64
+#define WAIT_NS 2000000000ull
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
-void sxl_mixed_free(sxl_ctx*) {}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// true when the phase of the given parity has completed; false on timeout
+// (which also raises *abort) or when another role raised *abort.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, bool honor_abort) {
+  if (mbar_try(bar, parity)) return true;
+  uint64_t t0 = gtimer();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 63u) == 0) {
+      if (honor_abort && *abort) return false;
+      if (gtimer() - t0 > WAIT_NS) {
+        *abort = 1;
+        return false;
+      }
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16, one CTA
+__device__ __forceinline__ void umma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes (64 16-bit elements), 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused here) = 16 B
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset = 1024 B
+  d |= (uint64_t)1 << 46;                    // descriptor version
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+// Instruction descriptor, kind::f16: fp32 accumulator, A/B fp16 (0) or bf16 (1),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_f16(bool bf16, int M, int N) {
+  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// ---------------------------------------------------------------------------
+// hi/lo storage
+template <bool BF16>
+struct HL;
+template <>
+struct HL<false> {
+  static __device__ __forceinline__ float f(uint16_t b) { return __half2float(__ushort_as_half(b)); }
+  static __device__ __forceinline__ uint16_t b(float v) { return __half_as_ushort(__float2half_rn(v)); }
+};
+template <>
+struct HL<true> {
+  static __device__ __forceinline__ float f(uint16_t b) {
+    return __bfloat162float(__ushort_as_bfloat16(b));
+  }
+  static __device__ __forceinline__ uint16_t b(float v) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+  }
+};
+#define LO_SCALE 4096.0f
+#define LO_INV (1.0f / 4096.0f)
+template <bool BF16>
+__device__ __forceinline__ float ld_hl(const uint16_t* hi, const uint16_t* lo, size_t i) {
+  return HL<BF16>::f(hi[i]) + HL<BF16>::f(lo[i]) * LO_INV;
+}
+template <bool BF16>
+__device__ __forceinline__ double ld_hl_d(const uint16_t* hi, const uint16_t* lo, size_t i) {
+  return (double)HL<BF16>::f(hi[i]) + (double)HL<BF16>::f(lo[i]) * (double)LO_INV;
+}
+template <bool BF16>
+__device__ __forceinline__ void st_hl(uint16_t* hi, uint16_t* lo, size_t i, double v) {
+  uint16_t h = HL<BF16>::b((float)v);
+  hi[i] = h;
+  lo[i] = HL<BF16>::b((float)((v - (double)HL<BF16>::f(h)) * (double)LO_SCALE));
+}
+
+// ---------------------------------------------------------------------------
+struct TcArgs {
+  int n, ntm, ntn, nk;
+  float alpha, beta, gamma;
+  const uint16_t* Ehi;
+  const uint16_t* Elo;
+  uint16_t* Chi;
+  uint16_t* Clo;
+  int sym;
+  int* err;
+};
+
+template <bool SPLIT>
+struct TcCfg {
+  static constexpr int STAGES = SPLIT ? 2 : 4;
+  static constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2;
+  static constexpr uint32_t B_BYTES = TC_BN * TC_BK * 2;
+  static constexpr uint32_t STAGE_BYTES = (A_BYTES + B_BYTES) * (SPLIT ? 2 : 1);
+  static constexpr uint32_t TMEM_COLS = SPLIT ? 512 : 256;
+  static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
+};
+
+template <bool BF16, bool SPLIT>
+__global__ void __launch_bounds__(192, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+              const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
+              TcArgs g) {
+  using Cfg = TcCfg<SPLIT>;
+  constexpr int STAGES = Cfg::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_bar;
+  __shared__ uint32_t s_tmem;
+  __shared__ volatile int s_abort;
+  __shared__ int s_issued, s_consumed;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int bz = blockIdx.y;
+  // grouped rasterization: bands of 16 row tiles sweep the column tiles
+  const int GROUP = 16;
+  const int t = blockIdx.x;
+  const int per_group = GROUP * g.ntn;
+  const int first_m = (t / per_group) * GROUP;
+  const int gsz = min(g.ntm - first_m, GROUP);
+  const int tm = first_m + (t % per_group) % gsz;
+  const int tn = (t % per_group) / gsz;
+  const int row0 = tm * TC_BM, col0 = tn * TC_BN;
+  if (g.sym && col0 + TC_BN - 1 < row0) return;  // owns no element with row <= col
+
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const uint32_t sbase = smem_u32(smem);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      mbar_init(smem_u32(&empty_bar[s]), 1);
+    }
+    mbar_init(smem_u32(&acc_bar), 1);
+    s_abort = 0;
+    s_issued = 0;
+    s_consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&s_tmem)),
+                 "r"(Cfg::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int kb = 0;
+      for (; kb < g.nk; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (kb >= STAGES &&
+            !mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u, &s_abort, true))
+          break;
+        const uint32_t fb = smem_u32(&full_bar[s]);
+        mbar_expect_tx(fb, Cfg::STAGE_BYTES);
+        const uint32_t st = sbase + s * Cfg::STAGE_BYTES;
+        const int kx = kb * TC_BK;
+        tma_load_2d(st, &mAh, fb, kx, bz * g.n + row0);
+        tma_load_2d(st + Cfg::A_BYTES, &mBh, fb, kx, bz * g.n + col0);
+        if (SPLIT) {
+          tma_load_2d(st + Cfg::A_BYTES + Cfg::B_BYTES, &mAl, fb, kx, bz * g.n + row0);
+          tma_load_2d(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES, &mBl, fb, kx, bz * g.n + col0);
+        }
+      }
+      s_issued = kb;
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_f16(BF16, TC_BM, TC_BN);
+      int kb = 0;
+      for (; kb < g.nk; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t ph = (kb / STAGES) & 1;
+        if (!mbar_wait(smem_u32(&full_bar[s]), ph, &s_abort, true)) break;
+        tc_fence_after();
+        const uint32_t st = sbase + s * Cfg::STAGE_BYTES;
+        const uint64_t dAh = sdesc_sw128(st);
+        const uint64_t dBh = sdesc_sw128(st + Cfg::A_BYTES);
+        const uint64_t dAl = sdesc_sw128(st + Cfg::A_BYTES + Cfg::B_BYTES);
+        const uint64_t dBl = sdesc_sw128(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+          const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+          const uint64_t adv = (uint64_t)(2 * kk);  // 16 elements = 32 bytes = 2 units
+          umma_f16(tmem, dAh + adv, dBh + adv, idesc, acc);
+          if (SPLIT) {
+            umma_f16(tmem + 256, dAh + adv, dBl + adv, idesc, acc);
+            umma_f16(tmem + 256, dAl + adv, dBh + adv, idesc, 1u);
+          }
+        }
+        umma_commit(smem_u32(&empty_bar[s]));
+      }
+      s_consumed = kb;
+      umma_commit(smem_u32(&acc_bar));
+    }
+  } else {
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int row = row0 + q * 32 + lane;
+    bool ok = mbar_wait(smem_u32(&acc_bar), 0, &s_abort, true);
+    ok = __all_sync(0xffffffffu, ok);
+    tc_fence_after();
+    if (ok) {
+      const size_t mat = (size_t)bz * g.n * g.n;
+      for (int cc = 0; cc < TC_BN; cc += 32) {
+        uint32_t a0[32], a1[32];
+        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)cc;
+        tmem_ld32(ta, a0);
+        if (SPLIT) tmem_ld32(ta + 256, a1);
+        tmem_wait_ld();
+        if (row < g.n) {
+          const size_t rb = mat + (size_t)row * g.n;
+#pragma unroll 4
+          for (int j = 0; j < 32; ++j) {
+            const int col = col0 + cc + j;
+            if (col >= g.n) break;
+            if (g.sym && row > col) continue;
+            float v = __uint_as_float(a0[j]);
+            if (SPLIT) v += __uint_as_float(a1[j]) * LO_INV;
+            double w = (double)g.alpha * (double)v;
+            if (g.Ehi) w += (double)g.beta * ld_hl_d<BF16>(g.Ehi, g.Elo, rb + col);
+            if (row == col) w += (double)g.gamma;
+            st_hl<BF16>(g.Chi, g.Clo, rb + col, w);
+            if (g.sym && row != col) st_hl<BF16>(g.Chi, g.Clo, mat + (size_t)col * g.n + row, w);
+          }
+        }
+      }
+    }
+  }
+
+  // teardown: on an abort, let in-flight copies and MMAs finish (bounded)
+  tc_fence_before();
+  __syncthreads();
+  if (s_abort) {
+    if (threadIdx.x == 0) {
+      atomicExch(g.err, 1);
+      for (int kb = s_consumed; kb < s_issued; ++kb)
+        mbar_wait(smem_u32(&full_bar[kb % STAGES]), (kb / STAGES) & 1, &s_abort, false);
+      mbar_wait(smem_u32(&acc_bar), 0, &s_abort, false);
+    }
+    __syncthreads();
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(Cfg::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side: tensor maps and launch
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static int* g_tc_err = nullptr;
+
+static int get_encode(sxl_ctx* c) {
+  if (g_encode) return SXL_OK;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e =
+      cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+    return sxl_fail(c, SXL_E_UNSUPPORTED, "cuTensorMapEncodeTiled not available");
+  g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  return SXL_OK;
+}
+
+static int make_map(sxl_ctx* c, CUtensorMap* m, const uint16_t* base, int n, int box_rows,
+                    bool bf16) {
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)(2 * (size_t)n)};
+  cuuint64_t strides[1] = {(cuuint64_t)n * 2};
+  cuuint32_t box[2] = {TC_BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                        2, (void*)base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return sxl_fail(c, SXL_E_CUDA, "cuTensorMapEncodeTiled failed");
+  return SXL_OK;
+}
+
+template <bool BF16, bool SPLIT>
+static int launch_tc(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a) {
+  using Cfg = TcCfg<SPLIT>;
+  static bool attr = false;
+  if (!attr) {
+    CUDA_TRY(c, cudaFuncSetAttribute(k_tc_gemm<BF16, SPLIT>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
+    attr = true;
+  }
+  dim3 grid(a.ntm * a.ntn, 2);
+  k_tc_gemm<BF16, SPLIT><<<grid, 192, Cfg::SMEM, c->st>>>(maps[0], maps[1], maps[2], maps[3], a);
+  ++g_sxl_launches;
+  return SXL_OK;
+}
+
+// C = alpha A B^T + beta E + gamma I for both spins; split selects the
+// three-product form.  Matrices are n x n with n % 64 == 0.
+int gemm_tc(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C, float alpha,
+            const MatH* E, float beta, float gamma, bool sym, bool split) {
+  const bool bf16 = c->p.precision == SXL_MIXED_BF16;
+  const int n = c->N;
+  CUtensorMap maps[4];
+  SXL_TRY(make_map(c, &maps[0], A.hi, n, TC_BM, bf16));
+  SXL_TRY(make_map(c, &maps[1], A.lo, n, TC_BM, bf16));
+  SXL_TRY(make_map(c, &maps[2], B.hi, n, TC_BN, bf16));
+  SXL_TRY(make_map(c, &maps[3], B.lo, n, TC_BN, bf16));
+  TcArgs a;
+  a.n = n;
+  a.ntm = (n + TC_BM - 1) / TC_BM;
+  a.ntn = (n + TC_BN - 1) / TC_BN;
+  a.nk = n / TC_BK;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.gamma = gamma;
+  a.Ehi = E ? E->hi : nullptr;
+  a.Elo = E ? E->lo : nullptr;
+  a.Chi = C.hi;
+  a.Clo = C.lo;
+  a.sym = sym ? 1 : 0;
+  a.err = g_tc_err;
+  c->n_gemm++;
+  if (bf16) return split ? launch_tc<true, true>(c, maps, a) : launch_tc<true, false>(c, maps, a);
+  return split ? launch_tc<false, true>(c, maps, a) : launch_tc<false, false>(c, maps, a);
+}
+
+// ---------------------------------------------------------------------------
+// elementwise kernels on (hi, lo) matrices
+template <bool BF16>
+__global__ void k_build_u_h(int nat, const double* __restrict__ H0, const double* __restrict__ shift,
+                            double mu, double scale, uint16_t* hi, uint16_t* lo) {
+  const int N = nat * NORB;
+  size_t total = (size_t)N * N;
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  int r = (int)(i / N), col = (int)(i % N);
+  double h = H0[i];
+  double u0 = scale * h, u1 = u0;
+  if (r == col) {
+    u0 = scale * (h + shift[r / NORB] - mu);
+    u1 = scale * (h + shift[nat + r / NORB] - mu);
+  }
+  st_hl<BF16>(hi, lo, i, u0);
+  st_hl<BF16>(hi, lo, total + i, u1);
+}
+
+template <bool BF16>
+__global__ void k_axpy_diag_h(size_t total, int n, uint16_t* ohi, uint16_t* olo, double a,
+                              const uint16_t* xhi, const uint16_t* xlo, double g) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  size_t e = i % ((size_t)n * n);
+  double v = a * ld_hl_d<BF16>(xhi, xlo, i);
+  if (e / n == e % n) v += g;
+  st_hl<BF16>(ohi, olo, i, v);
+}
+
+// out = a X + b (Y + Y^T) + cc (w_i + w_j) Z
+template <bool BF16>
+__global__ void k_symcombo_h(int n, uint16_t* ohi, uint16_t* olo, double a, const uint16_t* xhi,
+                             const uint16_t* xlo, double b, const uint16_t* yhi,
+                             const uint16_t* ylo, double cc, const double* w, const uint16_t* zhi,
+                             const uint16_t* zlo) {
+  const size_t bs = (size_t)n * n * blockIdx.z;
+  __shared__ double tile[32][33];
+  int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  int tx = threadIdx.x, ty = threadIdx.y;
+  if (yhi) {
+    for (int k = ty; k < 32; k += 8) {
+      int r = bx + k, col = by + tx;
+      tile[k][tx] = (r < n && col < n) ? ld_hl_d<BF16>(yhi, ylo, bs + (size_t)r * n + col) : 0.0;
+    }
+  }
+  __syncthreads();
+  const double* wv = w ? w + (size_t)n * blockIdx.z : nullptr;
+  for (int k = ty; k < 32; k += 8) {
+    int r = by + k, col = bx + tx;
+    if (r >= n || col >= n) continue;
+    size_t idx = bs + (size_t)r * n + col;
+    double v = 0.0;
+    if (xhi) v += a * ld_hl_d<BF16>(xhi, xlo, idx);
+    if (yhi) v += b * (ld_hl_d<BF16>(yhi, ylo, idx) + tile[tx][k]);
+    if (zhi) v += cc * (wv[r] + wv[col]) * ld_hl_d<BF16>(zhi, zlo, idx);
+    st_hl<BF16>(ohi, olo, idx, v);
+  }
+}
+
+template <bool BF16>
+__global__ void k_rowstats_h(int n, int rows, const uint16_t* hi, const uint16_t* lo, double* diag,
+                             double* rowsq) {
+  int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  int b = row / n, i = row % n;
+  size_t base = (size_t)b * n * n + (size_t)i * n;
+  double s = 0.0;
+  for (int j = lane; j < n; j += 32) {
+    double t = ld_hl_d<BF16>(hi, lo, base + j);
+    s += t * t;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    diag[row] = ld_hl_d<BF16>(hi, lo, base + i);
+    if (rowsq) rowsq[row] = s;
+  }
+}
+
+// out[0] = sum_ij H0_ij T_ij for spin s (deterministic two-stage)
+template <bool BF16>
+__global__ void k_dot_h_partial(long long len, const double* __restrict__ H0, const uint16_t* hi,
+                                const uint16_t* lo, double* part) {
+  __shared__ double sm[256];
+  double s = 0.0;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < len; i += 256LL * gridDim.x)
+    s += H0[i] * ld_hl_d<BF16>(hi, lo, i);
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+__global__ void k_sum_parts(int np, const double* part, double* out) {
+  __shared__ double sm[256];
+  double s = threadIdx.x < np ? part[threadIdx.x] : 0.0;
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = sm[0];
+}
+
+template <bool BF16>
+__global__ void k_diag2_h(int n, const uint16_t* hi, const uint16_t* lo, double* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * n) return;
+  int s = i / n, r = i % n;
+  out[i] = ld_hl_d<BF16>(hi, lo, (size_t)s * n * n + (size_t)r * n + r);
+}
+
+template <bool BF16>
+__global__ void k_d_from_t_h(size_t nn, const uint16_t* hi, const uint16_t* lo, double* D, int N) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  size_t e = i % ((size_t)N * N);
+  D[i] = ((e / N == e % N) ? 0.5 : 0.0) - 0.5 * ld_hl_d<BF16>(hi, lo, i);
+}
+
+// ---------------------------------------------------------------------------
+// dispatch helpers (BF16 template chosen at run time)
+#define DISPATCH(c, KERN, grid, block, smem, ...)                                   \
+  do {                                                                              \
+    if ((c)->p.precision == SXL_MIXED_BF16)                                         \
+      LAUNCH(KERN<true>, grid, block, smem, (c)->st, __VA_ARGS__);                  \
+    else                                                                            \
+      LAUNCH(KERN<false>, grid, block, smem, (c)->st, __VA_ARGS__);                 \
+  } while (0)
+
+static void symcombo_h(sxl_ctx* c, const MatH& out, double a, const MatH* X, double b,
+                       const MatH* Y, double cc, const double* w, const MatH* Z) {
+  int n = c->N;
+  dim3 grid((n + 31) / 32, (n + 31) / 32, 2), block(32, 8);
+  DISPATCH(c, k_symcombo_h, grid, block, 0, n, out.hi, out.lo, a, X ? X->hi : nullptr,
+           X ? X->lo : nullptr, b, Y ? Y->hi : nullptr, Y ? Y->lo : nullptr, cc, w,
+           Z ? Z->hi : nullptr, Z ? Z->lo : nullptr);
+}
+
+static void axpy_diag_h(sxl_ctx* c, const MatH& out, double a, const MatH& X, double g) {
+  size_t total = 2 * (size_t)c->N * c->N;
+  DISPATCH(c, k_axpy_diag_h, (unsigned)((total + 255) / 256), 256, 0, total, c->N, out.hi, out.lo,
+           a, X.hi, X.lo, g);
+}
+
+static int halloc(sxl_ctx* c, MatH* m) {
+  size_t n = 2 * (size_t)c->N * c->N;
+  m->hi = m->lo = nullptr;
+  if (cudaMalloc((void**)&m->hi, n * 2) != cudaSuccess ||
+      cudaMalloc((void**)&m->lo, n * 2) != cudaSuccess)
+    return sxl_fail(c, SXL_E_NOMEM, "cudaMalloc failed for a mixed-precision matrix");
+  CUDA_TRY(c, cudaMemsetAsync(m->hi, 0, n * 2, c->st));
+  CUDA_TRY(c, cudaMemsetAsync(m->lo, 0, n * 2, c->st));
+  return SXL_OK;
+}
+static void hfree(MatH& m) {
+  if (m.hi) cudaFree(m.hi);
+  if (m.lo) cudaFree(m.lo);
+  m.hi = m.lo = nullptr;
+}
+
+int sxl_mixed_supported(sxl_ctx* c) {
+  if (c->N % 64 != 0)
+    return sxl_fail(c, SXL_E_ARG, "mixed precision needs 9 N_at to be a multiple of 64");
+  int dev = 0;
+  CUDA_TRY(c, cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  CUDA_TRY(c, cudaGetDeviceProperties(&prop, dev));
+  if (prop.major < 10) return sxl_fail(c, SXL_E_UNSUPPORTED, "tcgen05 needs compute capability 10.x");
+  SXL_TRY(get_encode(c));
+  if (!g_tc_err) {
+    CUDA_TRY(c, cudaMalloc((void**)&g_tc_err, sizeof(int)));
+    CUDA_TRY(c, cudaMemset(g_tc_err, 0, sizeof(int)));
+  }
+  MatH* ms[] = {&c->hU, &c->hS, &c->hQ, &c->hX0, &c->hX1, &c->hP, &c->hSm, &c->hdTa, &c->hdTb, &c->hG1};
+  for (MatH* m : ms) SXL_TRY(halloc(c, m));
+  return SXL_OK;
+}
+
+void sxl_mixed_free(sxl_ctx* c) {
+  MatH* ms[] = {&c->hU, &c->hS, &c->hQ, &c->hX0, &c->hX1, &c->hP, &c->hSm, &c->hdTa, &c->hdTb, &c->hG1};
+  for (MatH* m : ms) hfree(*m);
+  for (MatH& m : c->hT) hfree(m);
+  for (MatH& m : c->hY) hfree(m);
+  c->hT.clear();
+  c->hY.clear();
+}
+
+int tc_error_flag(sxl_ctx* c, int* flag) {
+  *flag = 0;
+  if (!g_tc_err) return SXL_OK;
+  CUDA_TRY(c, cudaMemcpyAsync(flag, g_tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return SXL_OK;
+}
+
+static int ensure_chain_h(sxl_ctx* c, int nr) {
+  while ((int)c->hT.size() < nr + 1) {
+    MatH m;
+    SXL_TRY(halloc(c, &m));
+    c->hT.push_back(m);
+  }
+  while ((int)c->hY.size() < nr) {
+    MatH m;
+    SXL_TRY(halloc(c, &m));
+    c->hY.push_back(m);
+  }
+  return SXL_OK;
+}
+
+static double tanh5(double u) { return u - u * u * u / 3.0 + 2.0 * std::pow(u, 5) / 15.0; }
+
+// Same recursion as the fp64 form (see api.cu), on tensor cores.
+int foe_mixed(sxl_ctx* c, double mu, double* stats_dev) {
+  const int N = c->N, nr = c->nr;
+  SXL_TRY(ensure_chain_h(c, nr));
+  const bool split = true;
+  c->umax = c->scale * std::max(std::fabs(c->lam_max - mu), std::fabs(mu - c->lam_min));
+  size_t total = (size_t)N * N;
+  DISPATCH(c, k_build_u_h, (unsigned)((total + 255) / 256), 256, 0, c->nat, c->H0, c->shift, mu,
+           c->scale, c->hU.hi, c->hU.lo);
+  SXL_TRY(gemm_tc(c, c->hU, c->hU, c->hS, 1.f, nullptr, 0.f, 0.f, true, split));
+  SXL_TRY(gemm_tc(c, c->hS, c->hS, c->hQ, (float)(2.0 / 15.0), &c->hS, (float)(-1.0 / 3.0), 1.f,
+                  true, split));
+  SXL_TRY(gemm_tc(c, c->hU, c->hQ, c->hT[0], 1.f, nullptr, 0.f, 0.f, true, split));
+  double t = std::min(tanh5(c->umax), 1.0);
+  const double tol = 1e-9;
+  c->ns_iters.assign(nr, 0);
+  for (int k = 0; k < nr; ++k) {
+    const MatH& Sq = c->hSm;
+    SXL_TRY(gemm_tc(c, c->hT[k], c->hT[k], Sq, 1.f, nullptr, 0.f, 0.f, true, split));
+    double s = t * t;
+    double ci = 2.0 / (2.0 + s);
+    double e = s / (2.0 + s);
+    e *= e;
+    int j = 0;
+    while (e > tol && j < 12) { e *= e; ++j; }
+    c->ns_iters[k] = j;
+    const MatH* cur = (j == 0) ? &c->hY[k] : &c->hX0;
+    axpy_diag_h(c, *cur, -ci * ci, Sq, 2.0 * ci - ci * ci);
+    for (int it = 0; it < j; ++it) {
+      const MatH* nxt = (it == j - 1) ? &c->hY[k] : (cur == &c->hX0 ? &c->hX1 : &c->hX0);
+      SXL_TRY(gemm_tc(c, *cur, Sq, c->hP, 1.f, cur, 1.f, 0.f, false, split));
+      SXL_TRY(gemm_tc(c, c->hP, *cur, *nxt, -1.f, cur, 2.f, 0.f, true, split));
+      cur = nxt;
+    }
+    SXL_TRY(gemm_tc(c, c->hT[k], c->hY[k], c->hT[k + 1], 2.f, nullptr, 0.f, 0.f, true, split));
+    t = 2.0 * t / (1.0 + t * t);
+  }
+  int wpb = 8, rows = 2 * N;
+  DISPATCH(c, k_rowstats_h, (rows + wpb - 1) / wpb, 32 * wpb, 0, N, rows, c->hT[nr].hi,
+           c->hT[nr].lo, c->diagT, c->rowsq);
+  small_kernels_density(c, c->q, stats_dev);
+  return SXL_OK;
+}
+
+int dmpt_mixed(sxl_ctx* c, const double* du) {
+  const int N = c->N, nr = c->nr;
+  const bool split = true;
+  const MatH& dS = c->hSm;
+  symcombo_h(c, dS, 0.0, nullptr, 0.0, nullptr, 1.0, du, &c->hU);
+  SXL_TRY(gemm_tc(c, dS, c->hS, c->hG1, 1.f, nullptr, 0.f, 0.f, false, split));
+  symcombo_h(c, c->hP, -1.0 / 3.0, &dS, 2.0 / 15.0, &c->hG1, 0.0, nullptr, nullptr);
+  SXL_TRY(gemm_tc(c, c->hU, c->hP, c->hG1, 1.f, nullptr, 0.f, 0.f, false, split));
+  const MatH* dA = &c->hdTa;
+  const MatH* dB = &c->hdTb;
+  symcombo_h(c, *dA, 0.0, nullptr, 0.5, &c->hG1, 0.5, du, &c->hQ);
+  for (int k = 0; k < nr; ++k) {
+    SXL_TRY(gemm_tc(c, c->hT[k], *dA, c->hP, 1.f, nullptr, 0.f, 0.f, false, split));
+    symcombo_h(c, c->hSm, 0.0, nullptr, 1.0, &c->hP, 0.0, nullptr, nullptr);
+    SXL_TRY(gemm_tc(c, c->hT[k + 1], c->hSm, c->hG1, -0.5f, dA, 1.f, 0.f, false, split));
+    SXL_TRY(gemm_tc(c, c->hG1, c->hY[k], *dB, 2.f, nullptr, 0.f, 0.f, true, split));
+    std::swap(dA, dB);
+  }
+  DISPATCH(c, k_diag2_h, (2 * N + 255) / 256, 256, 0, N, dA->hi, dA->lo, c->diagT + 2 * N);
+  return SXL_OK;
+}
+
+void dot_h0_t_mixed(sxl_ctx* c, int spin, double* out) {
+  const size_t nn = (size_t)c->N * c->N;
+  const MatH& T = c->hT[c->nr];
+  DISPATCH(c, k_dot_h_partial, 128, 256, 0, (long long)nn, c->H0, T.hi + spin * nn, T.lo + spin * nn,
+           c->red + 2048);
+  LAUNCH(k_sum_parts, 1, 256, 0, c->st, 128, c->red + 2048, out);
+}
+
+void density_matrix_mixed(sxl_ctx* c, double* D) {
+  size_t nn = 2 * (size_t)c->N * c->N;
+  const MatH& T = c->hT[c->nr];
+  DISPATCH(c, k_d_from_t_h, (unsigned)((nn + 255) / 256), 256, 0, nn, T.hi, T.lo, D, c->N);
+}
+
+// standalone product for tests: C = A B^T on (hi, lo) inputs built from fp64
+template <bool BF16>
+__global__ void k_split_f64(size_t n, const double* x, uint16_t* hi, uint16_t* lo) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) st_hl<BF16>(hi, lo, i, x[i]);
+}
+template <bool BF16>
+__global__ void k_join_f64(size_t n, const uint16_t* hi, const uint16_t* lo, double* x) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) x[i] = ld_hl_d<BF16>(hi, lo, i);
+}
+
+int mixed_gemm_test(sxl_ctx* c, const double* A, const double* B, const double* E, double* C,
+                    double alpha, double beta, double gamma, int sym, int split) {
+  size_t nn = 2 * (size_t)c->N * c->N;
+  unsigned g = (unsigned)((nn + 255) / 256);
+  DISPATCH(c, k_split_f64, g, 256, 0, nn, A, c->hU.hi, c->hU.lo);
+  DISPATCH(c, k_split_f64, g, 256, 0, nn, B, c->hS.hi, c->hS.lo);
+  if (E) DISPATCH(c, k_split_f64, g, 256, 0, nn, E, c->hQ.hi, c->hQ.lo);
+  SXL_TRY(gemm_tc(c, c->hU, c->hS, c->hG1, (float)alpha, E ? &c->hQ : nullptr, (float)beta,
+                  (float)gamma, sym != 0, split != 0));
+  DISPATCH(c, k_join_f64, g, 256, 0, nn, c->hG1.hi, c->hG1.lo, C);
+  return SXL_OK;
+}

@@ -272,6 +272,21 @@ __device__ inline double tsum_at<TsumF64>(const TsumF64& ts, size_t idx) {
   return ts.T[idx] + ts.T[ts.nn + idx];
 }
 
+template <bool BF16>
+struct TsumH {
+  const uint16_t* hi;
+  const uint16_t* lo;
+  size_t nn;
+};
+template <>
+__device__ inline double tsum_at<TsumH<false>>(const TsumH<false>& ts, size_t idx) {
+  return hl_value<false>(ts.hi, ts.lo, idx) + hl_value<false>(ts.hi, ts.lo, ts.nn + idx);
+}
+template <>
+__device__ inline double tsum_at<TsumH<true>>(const TsumH<true>& ts, size_t idx) {
+  return hl_value<true>(ts.hi, ts.lo, idx) + hl_value<true>(ts.hi, ts.lo, ts.nn + idx);
+}
+
 template <class TS>
 __global__ void __launch_bounds__(256) k_forces(int nat, const double* __restrict__ R,
                                                 ModelConst mc, TS ts,
@@ -355,6 +370,15 @@ __global__ void __launch_bounds__(256) k_forces(int nat, const double* __restric
 void launch_forces(sxl_ctx* c, const double* R, const double* n, const double* qspin,
                    double* F, double* erep_atom) {
   ModelConst mc = model_const(c->p);
-  TsumF64 ts{c->T[c->nr], (size_t)c->N * c->N};
-  LAUNCH(k_forces<TsumF64>, c->nat, 256, 0, c->st, c->nat, R, mc, ts, n, qspin, F, erep_atom);
+  const size_t nn = (size_t)c->N * c->N;
+  if (c->p.precision == SXL_FP64) {
+    TsumF64 ts{c->T[c->nr], nn};
+    LAUNCH(k_forces<TsumF64>, c->nat, 256, 0, c->st, c->nat, R, mc, ts, n, qspin, F, erep_atom);
+  } else if (c->p.precision == SXL_MIXED_BF16) {
+    TsumH<true> ts{c->hT[c->nr].hi, c->hT[c->nr].lo, nn};
+    LAUNCH(k_forces<TsumH<true>>, c->nat, 256, 0, c->st, c->nat, R, mc, ts, n, qspin, F, erep_atom);
+  } else {
+    TsumH<false> ts{c->hT[c->nr].hi, c->hT[c->nr].lo, nn};
+    LAUNCH(k_forces<TsumH<false>>, c->nat, 256, 0, c->st, c->nat, R, mc, ts, n, qspin, F, erep_atom);
+  }
 }

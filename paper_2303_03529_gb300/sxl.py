@@ -64,6 +64,7 @@ EXPORTS = {
     "xlbomd_step": (_i, [_p, _i, _p]),
     "scf_solve": (_i, [_p, _p, _p, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
     "sxl_info": (_i, [_p, _p]),
+    "sxl_mixed_gemm": (_i, [_p, _p, _p, _p, _p, _d, _d, _d, _i, _i]),
 }
 
 _lib = None
@@ -277,6 +278,18 @@ class Context:
                                        float(tol), int(max_iter), ctypes.byref(it),
                                        ctypes.byref(rms)), "scf_solve")
         return n, it.value, rms.value
+
+    def mixed_gemm(self, A, B, E=None, alpha=1.0, beta=0.0, gamma=0.0, sym=False, split=True):
+        """C = alpha A B^T + beta E + gamma I on the tensor-core path (2 x N x N)."""
+        A, B = self._dev(A), self._dev(B)
+        E = self._dev(E) if E is not None else None
+        C = self._new(2, self.N, self.N)
+        nn = 2 * self.N * self.N
+        self._check(self.lib.sxl_mixed_gemm(self.h, _ptr(A, nn), _ptr(B, nn),
+                                            _ptr(E, nn) if E is not None else None, _ptr(C),
+                                            float(alpha), float(beta), float(gamma), int(sym),
+                                            int(split)), "sxl_mixed_gemm")
+        return C
 
     def info(self):
         out = np.zeros(7)

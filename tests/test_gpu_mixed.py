@@ -1,0 +1,93 @@
+"""Mixed-precision (tcgen05, fp16 / bf16 with fp32 accumulation) path.
+
+1. The tensor-core GEMM against an fp64 product of the same inputs, at
+   N = 1152 (9 row tiles of 128, 4.5 column tiles of 256: a ragged edge),
+   in plain, split, symmetric and epilogue (beta E + gamma I) modes.  Bounds
+   follow from the arithmetic: inputs rounded to hi (fp16: 2^-11, bf16: 2^-8
+   relative) for the plain form, hi + lo 2^-12 for the split form, fp32
+   accumulation over K = 1152 terms.
+2. The mixed density (q, mu) and response q_v at 128 atoms against the FP64
+   oracle, with the tolerance of the mixed form: 1e-4 e on charges/spins.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import electronic, energy  # noqa: E402
+from paper_2303_03529_gb300 import workload as wl  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def sxl():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_03529_gb300 import sxl as s
+    return s
+
+
+def _sym(rng, n, scale=1.0):
+    a = rng.normal(size=(n, n)) * scale / np.sqrt(n)
+    return 0.5 * (a + a.T)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_tc_gemm_against_fp64(sxl, prec):
+    w = wl.fe128()
+    ctx = sxl.Context(w.params, w.n_atoms, w.cell, prec)
+    n = w.n_orb
+    rng = np.random.default_rng(0)
+    A = np.stack([_sym(rng, n), _sym(rng, n)])
+    B = np.stack([_sym(rng, n), _sym(rng, n)])
+    E = np.stack([_sym(rng, n), _sym(rng, n)])
+    ref = np.einsum("bij,bkj->bik", A, B)
+    eps_hi = 2.0 ** -11 if prec == "fp16" else 2.0 ** -8
+    eps_split = 2.0 ** -22 if prec == "fp16" else 2.0 ** -16
+    scale = np.abs(ref).max()
+    # plain: hi x hi
+    C = ctx.mixed_gemm(A, B, split=False).cpu().numpy()
+    err = np.abs(C - ref).max() / scale
+    assert err < 20 * eps_hi, err
+    # split: hi x hi + (hi x lo + lo x hi) 2^-12
+    C = ctx.mixed_gemm(A, B, split=True).cpu().numpy()
+    err = np.abs(C - ref).max() / scale
+    assert err < 20 * max(eps_split, 2.0 ** -21), err
+    # symmetric product with epilogue: 0.5 A A^T - 2 E + 3 I, mirrored tiles
+    ref2 = 0.5 * np.einsum("bij,bkj->bik", A, A) - 2.0 * E + 3.0 * np.eye(n)
+    C = ctx.mixed_gemm(A, A, E, alpha=0.5, beta=-2.0, gamma=3.0, sym=True, split=True)
+    C = C.cpu().numpy()
+    np.testing.assert_array_equal(C, np.transpose(C, (0, 2, 1)))
+    err = np.abs(C - ref2).max() / np.abs(ref2).max()
+    assert err < 20 * max(eps_split, 2.0 ** -21), err
+    ctx.close()
+
+
+@pytest.fixture(scope="module")
+def dens128():
+    w = wl.fe128()
+    return w, electronic.density(w.R, w.cell, w.n0, w.params)
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_mixed_density_and_response(sxl, dens128, prec):
+    w, d = dens128
+    ctx = sxl.Context(w.params, w.n_atoms, w.cell, prec, mu_tol=1e-7)
+    q, mu = ctx.density(w.R, w.n0)
+    q = q.cpu().numpy()
+    err_q = np.abs(q - d.q).max()
+    err_m = np.abs((q[:128] - q[128:]) - d.spin).max()
+    print(f"{prec}: |dq| {err_q:.2e} |dm| {err_m:.2e} |dmu| {abs(mu - d.mu):.2e}")
+    tol = 1e-4 if prec == "fp16" else 2e-3
+    assert err_q < tol and err_m < tol
+    v = wl.random_direction(128, 11)
+    qv, _ = ctx.response(v)
+    qv_o, _ = d.response(v)
+    rel = np.abs(qv.cpu().numpy() - qv_o).max() / np.abs(qv_o).max()
+    print(f"{prec}: response rel err {rel:.2e}")
+    assert rel < (1e-3 if prec == "fp16" else 2e-2)
+    F, _ = ctx.forces(w.R, w.n0, energies=False)
+    err_f = np.abs(F.cpu().numpy() - energy.forces(d, w.R, w.cell)).max()
+    print(f"{prec}: |dF| {err_f:.2e}")
+    assert err_f < (1e-3 if prec == "fp16" else 2e-2)
+    ctx.close()
