@@ -84,6 +84,8 @@ typedef struct {
                                 foe_steps == 0 (0 = 0.25)                     */
   int    mu_max_iter;        /* cap on chemical-potential Newton passes (0 = 30) */
   double mu_tol;             /* |sum Tr D - N_e| tolerance (0 = 1e-10)         */
+  int    scf_keep_k0;        /* scf_solve: 0 = build the exact K0 = J^{-1} when the
+                                kernel mixer starts, 1 = keep the installed K0 */
 } sxl_params;
 
 /* Create a context bound to the current CUDA device and `stream` (a
@@ -152,6 +154,13 @@ int sxl_set_state_host(sxl_ctx* ctx, const double* R_host, const double* V_host,
 int sxl_get_state_host(sxl_ctx* ctx, double* R_host, double* V_host,
                        double* nhist_host, double* mu_host);
 
+/* Forces and Kf = K (q - n) belonging to the context state (host arrays:
+ * N_at x 3 and 2 N_at).  Setting them after sxl_set_state_host marks the
+ * state as evaluated, so xlbomd_step does not recompute them; together with
+ * the state setters this moves the complete MD state through host memory. */
+int sxl_set_derived_host(sxl_ctx* ctx, const double* F_host, const double* Kf_host);
+int sxl_get_derived_host(sxl_ctx* ctx, double* F_host, double* Kf_host);
+
 /* Stage a9 (Eq. Integration): `nsteps` sXL-BOMD steps from the context
  * state.  stats_host (may be NULL) receives nsteps x 4 doubles
  * [E_tot (eV), T (K), RMS(q - n), mu (eV)] after each step; energies are
@@ -177,6 +186,18 @@ int scf_solve(sxl_ctx* ctx, const double* R_dev, double* n_dev, double tol,
  * Needs a context created with SXL_MIXED_FP16 or SXL_MIXED_BF16. */
 int sxl_mixed_gemm(sxl_ctx* ctx, const double* A_dev, const double* B_dev, const double* E_dev,
                    double* C_dev, double alpha, double beta, double gamma, int sym, int split);
+
+/* Device-time counters (CUDA events on the context stream) accumulated over
+ * xlbomd_step calls: out[0] steps, [1] density ms, [2] forces ms, [3] Krylov
+ * ms, [4] Krylov ranks, [5] tensor-core GEMM launches timed, [6] their total
+ * ms, [7] tensor-core MMA flops issued (whole tiles, three products per k
+ * step in split form), [8] tensor-core flops the owned outputs need (2 N per
+ * owned output element times the number of products), [9] fp32-equivalent
+ * flops (2 N per owned output element).
+ * GEMM launches are timed only after sxl_enable_gemm_timing(ctx, 1).
+ * reset = 1 clears the counters after reading. */
+int sxl_timers(sxl_ctx* ctx, double* out10, int reset);
+int sxl_enable_gemm_timing(sxl_ctx* ctx, int on);
 
 /* Diagnostics of the last density: [mu, N(mu), foe_steps, lambda_min,
  * lambda_max, GEMM launches so far, own kernel launches so far]. */

@@ -16,6 +16,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 int sxl_fail(sxl_ctx* c, int code, const std::string& msg) {
@@ -36,6 +38,54 @@ static int dalloc(sxl_ctx* c, double** p, size_t n) {
 }
 
 static double tanh5(double u) { return u - u * u * u / 3.0 + 2.0 * std::pow(u, 5) / 15.0; }
+
+// ---------------------------------------------------------------------------
+cudaEvent_t ev_get(sxl_ctx* c) {
+  if (!c->ev_free.empty()) {
+    cudaEvent_t e = c->ev_free.back();
+    c->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Accumulates the elapsed times of recorded event pairs (the stream must
+// have been synchronized past them) and recycles the events.
+void ev_resolve(sxl_ctx* c) {
+  for (auto& p : c->ev_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      c->tc_launches += 1;
+      c->tc_ms += ms;
+      c->tc_mma_flops += p.mma_flops;
+      c->tc_alg_flops += p.alg_flops;
+      c->tc_f32_flops += p.f32_flops;
+    }
+    c->ev_free.push_back(p.a);
+    c->ev_free.push_back(p.b);
+  }
+  c->ev_pending.clear();
+  for (auto& p : c->ph_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      int id = (int)p.mma_flops;
+      if (id == 0) c->tm_density += ms;
+      else if (id == 1) c->tm_forces += ms;
+      else if (id == 2) { c->tm_krylov += ms; c->tm_ranks += p.alg_flops; }
+    }
+    c->ev_free.push_back(p.a);
+    c->ev_free.push_back(p.b);
+  }
+  c->ph_pending.clear();
+}
+
+static cudaEvent_t phase_mark(sxl_ctx* c) {
+  cudaEvent_t e = ev_get(c);
+  cudaEventRecord(e, c->st);
+  return e;
+}
 
 // ---------------------------------------------------------------------------
 static int ensure_chain(sxl_ctx* c, int nr) {
@@ -174,7 +224,11 @@ static int density(sxl_ctx* c, const double* R, const double* n, double mu_guess
   double mu = std::isfinite(mu_guess) ? mu_guess : 0.5 * (c->lam_min + c->lam_max);
   mu = std::min(std::max(mu, lo), hi);
   const int maxit = c->p.mu_max_iter > 0 ? c->p.mu_max_iter : 30;
-  const double tol = c->p.mu_tol > 0 ? c->p.mu_tol : 1e-10;
+  // default tolerance: fp64 1e-10 e; mixed forms 1e-6 N_e (their trace noise
+  // is about sqrt(2N) 1e-6, and a charge error dN moves q_I by about dN / N_at)
+  const double tol = c->p.mu_tol > 0 ? c->p.mu_tol
+                                     : (c->p.precision == SXL_FP64 ? 1e-10 : 1e-6 * Ne);
+  const bool dbg = getenv("SXL_DEBUG") != nullptr;
   double* stats = c->red + 16;
   const bool mixed = c->p.precision != SXL_FP64;
   for (int it = 0;; ++it) {
@@ -187,7 +241,11 @@ static int density(sxl_ctx* c, const double* R, const double* n, double mu_guess
       if (flag) return sxl_fail(c, SXL_E_CUDA, "tensor-core GEMM reported a wait timeout");
     }
     double Nmu = c->hred[0], dN = c->hred[1];
+    if (dbg)
+      fprintf(stderr, "[sxl] mu pass %d: mu %.12f N %.10f dN/dmu %.6e nr %d umax %.3f\n", it, mu,
+              Nmu, dN, c->nr, c->umax);
     if (!std::isfinite(Nmu) || !std::isfinite(dN)) return sxl_fail(c, SXL_E_NAN, "non-finite density");
+    c->last_N = Nmu;
     double err = Nmu - Ne;
     if (std::fabs(err) < tol) break;
     if (it + 1 >= maxit)
@@ -342,6 +400,9 @@ int sxl_create(const sxl_params* prm, void* stream, sxl_ctx** out) {
   c->nr = 0; c->nr_cap = 0;
   c->lam_min = 0; c->lam_max = 0;
   c->n_gemm = 0;
+  c->time_tc = false;
+  c->tm_steps = c->tm_density = c->tm_forces = c->tm_krylov = c->tm_ranks = 0;
+  c->tc_launches = c->tc_ms = c->tc_mma_flops = c->tc_alg_flops = c->tc_f32_flops = 0;
   if (p.precision != SXL_FP64) {
     // the mixed-precision chain is provided by the tensor-core path
     int r = sxl_mixed_supported(c);
@@ -388,6 +449,8 @@ int sxl_destroy(sxl_ctx* c) {
   for (double* p : c->T) cudaFree(p);
   for (double* p : c->Y) cudaFree(p);
   sxl_mixed_free(c);
+  ev_resolve(c);
+  for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
   if (c->hred) cudaFreeHost(c->hred);
   delete c;
   return SXL_OK;
@@ -560,9 +623,18 @@ int sxl_get_state_host(sxl_ctx* c, double* R, double* V, double* nh, double* mu)
 static int evaluate(sxl_ctx* c, double* en) {
   const double* n = c->nhist + (size_t)c->hist_head * c->n2;
   c->have_density = false;
+  // each phase gets its own start/end event pair (events are recycled per pair)
+  cudaEvent_t d0 = phase_mark(c);
   SXL_TRY(density(c, c->R, n, c->mu));
+  cudaEvent_t d1 = phase_mark(c), f0 = phase_mark(c);
   SXL_TRY(eval_forces(c, c->R, n, c->F, en));
-  SXL_TRY(krylov(c, n, c->p.krylov_rank, 0.0, c->Kf, nullptr, nullptr));
+  cudaEvent_t f1 = phase_mark(c), k0 = phase_mark(c);
+  int rank = 0;
+  SXL_TRY(krylov(c, n, c->p.krylov_rank, 0.0, c->Kf, nullptr, &rank));
+  cudaEvent_t k1 = phase_mark(c);
+  c->ph_pending.push_back({d0, d1, 0.0, 0.0, 0.0});
+  c->ph_pending.push_back({f0, f1, 1.0, 0.0, 0.0});
+  c->ph_pending.push_back({k0, k1, 2.0, (double)rank, 0.0});
   c->evaluated = true;
   return SXL_OK;
 }
@@ -595,6 +667,8 @@ int xlbomd_step(sxl_ctx* c, int nsteps, double* stats) {
     }
   }
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  c->tm_steps += nsteps;
+  ev_resolve(c);
   return SXL_OK;
 }
 
@@ -619,7 +693,7 @@ int scf_solve(sxl_ctx* c, const double* R, double* n, double tol, int max_iter, 
       continue;
     }
     if (!k0) {
-      SXL_TRY(build_exact_k0(c, nullptr));
+      if (!c->p.scf_keep_k0) SXL_TRY(build_exact_k0(c, nullptr));
       k0 = true;
     }
     SXL_TRY(krylov(c, n, c->p.krylov_rank, 0.1, c->Kf, nullptr, nullptr));
@@ -644,10 +718,56 @@ int sxl_mixed_gemm(sxl_ctx* c, const double* A, const double* B, const double* E
   return SXL_OK;
 }
 
+int sxl_enable_gemm_timing(sxl_ctx* c, int on) {
+  if (!c) return SXL_E_ARG;
+  c->time_tc = on != 0;
+  return SXL_OK;
+}
+
+int sxl_timers(sxl_ctx* c, double* out, int reset) {
+  if (!c || !out) return SXL_E_ARG;
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  ev_resolve(c);
+  out[0] = c->tm_steps;
+  out[1] = c->tm_density;
+  out[2] = c->tm_forces;
+  out[3] = c->tm_krylov;
+  out[4] = c->tm_ranks;
+  out[5] = c->tc_launches;
+  out[6] = c->tc_ms;
+  out[7] = c->tc_mma_flops;
+  out[8] = c->tc_alg_flops;
+  out[9] = c->tc_f32_flops;
+  if (reset) {
+    c->tm_steps = c->tm_density = c->tm_forces = c->tm_krylov = c->tm_ranks = 0;
+    c->tc_launches = c->tc_ms = c->tc_mma_flops = c->tc_alg_flops = c->tc_f32_flops = 0;
+  }
+  return SXL_OK;
+}
+
+int sxl_set_derived_host(sxl_ctx* c, const double* F, const double* Kf) {
+  if (!c || !F || !Kf) return SXL_E_ARG;
+  if (!c->state_ready) return sxl_fail(c, SXL_E_STATE, "no MD state: call sxl_set_state first");
+  CUDA_TRY(c, cudaMemcpyAsync(c->F, F, 3 * c->nat * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CUDA_TRY(c, cudaMemcpyAsync(c->Kf, Kf, c->n2 * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  c->evaluated = true;
+  return SXL_OK;
+}
+
+int sxl_get_derived_host(sxl_ctx* c, double* F, double* Kf) {
+  if (!c || !F || !Kf) return SXL_E_ARG;
+  if (!c->evaluated) return sxl_fail(c, SXL_E_STATE, "state not evaluated yet");
+  CUDA_TRY(c, cudaMemcpyAsync(F, c->F, 3 * c->nat * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(c, cudaMemcpyAsync(Kf, c->Kf, c->n2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return SXL_OK;
+}
+
 int sxl_info(sxl_ctx* c, double* out) {
   if (!c || !out) return SXL_E_ARG;
   out[0] = c->mu;
-  out[1] = 0.0;
+  out[1] = c->last_N;
   out[2] = c->nr;
   out[3] = c->lam_min;
   out[4] = c->lam_max;

@@ -58,6 +58,7 @@ struct sxl_ctx {
   double scale;           // U = scale (H - mu I), scale = beta / 2^(nr+1)
   double umax;            // bound on |eig(U)|
   double lam_min, lam_max;
+  double last_N;          // N(mu) of the last expansion pass
   double *U, *S, *Q, *X0, *X1, *P, *Sm, *dTa, *dTb, *G1;
   std::vector<double*> T, Y;
   std::vector<int> ns_iters;  // Newton-Schulz iterations used at each step
@@ -76,7 +77,23 @@ struct sxl_ctx {
   int *ipiv;
 
   unsigned long long n_gemm;
+
+  // device-time accounting (CUDA events on the context stream)
+  struct EvPair {
+    cudaEvent_t a, b;
+    double mma_flops, alg_flops, f32_flops;
+  };
+  bool time_tc;                      // per-launch timing of the tensor-core GEMM
+  std::vector<cudaEvent_t> ev_free;  // recycled events
+  std::vector<EvPair> ev_pending;    // recorded, not yet resolved
+  double tm_steps, tm_density, tm_forces, tm_krylov, tm_ranks;
+  double tc_launches, tc_ms, tc_mma_flops, tc_alg_flops, tc_f32_flops;
+  std::vector<EvPair> ph_pending;    // phase events: mma_flops = phase id
 };
+
+// event helpers (api.cu)
+cudaEvent_t ev_get(sxl_ctx* c);
+void ev_resolve(sxl_ctx* c);
 
 // ---- error helpers ---------------------------------------------------------
 int sxl_fail(sxl_ctx* c, int code, const std::string& msg);

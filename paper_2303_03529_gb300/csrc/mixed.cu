@@ -397,8 +397,27 @@ static int launch_tc(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a) {
     attr = true;
   }
   dim3 grid(a.ntm * a.ntn, 2);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->time_tc) {
+    e0 = ev_get(c);
+    e1 = ev_get(c);
+    CUDA_TRY(c, cudaEventRecord(e0, c->st));
+  }
   k_tc_gemm<BF16, SPLIT><<<grid, 192, Cfg::SMEM, c->st>>>(maps[0], maps[1], maps[2], maps[3], a);
   ++g_sxl_launches;
+  if (c->time_tc) {
+    CUDA_TRY(c, cudaEventRecord(e1, c->st));
+    // tiles actually computed (symmetric launches skip tiles below the diagonal)
+    double tiles = 0;
+    for (int tm = 0; tm < a.ntm; ++tm)
+      for (int tn = 0; tn < a.ntn; ++tn)
+        if (!a.sym || tn * TC_BN + TC_BN - 1 >= tm * TC_BM) tiles += 1;
+    double n = a.n;
+    double mma = 2.0 * tiles * 2.0 * TC_BM * TC_BN * n * (SPLIT ? 3.0 : 1.0);
+    double owned = a.sym ? n * (n + 1) / 2 : n * n;
+    double f32 = 2.0 * 2.0 * owned * n;  // both spins, 2 n flops per owned element
+    c->ev_pending.push_back({e0, e1, mma, f32 * (SPLIT ? 3.0 : 1.0), f32});
+  }
   return SXL_OK;
 }
 

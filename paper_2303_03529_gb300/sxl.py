@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
         ("krylov_rank", _i), ("kmax", _i),
         ("kappa", _d), ("alpha", _d), ("c", _d * 10),
         ("precision", _i), ("foe_steps", _i), ("foe_u_max", _d),
-        ("mu_max_iter", _i), ("mu_tol", _d),
+        ("mu_max_iter", _i), ("mu_tol", _d), ("scf_keep_k0", _i),
     ]
 
 
@@ -65,6 +65,10 @@ EXPORTS = {
     "scf_solve": (_i, [_p, _p, _p, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
     "sxl_info": (_i, [_p, _p]),
     "sxl_mixed_gemm": (_i, [_p, _p, _p, _p, _p, _d, _d, _d, _i, _i]),
+    "sxl_set_derived_host": (_i, [_p, _p, _p]),
+    "sxl_get_derived_host": (_i, [_p, _p, _p]),
+    "sxl_timers": (_i, [_p, _p, _i]),
+    "sxl_enable_gemm_timing": (_i, [_p, _i]),
 }
 
 _lib = None
@@ -91,7 +95,7 @@ class SxlError(RuntimeError):
 
 
 def make_params(mp, n_atoms: int, cell, precision="fp64", foe_steps=0, foe_u_max=0.0,
-                mu_tol=0.0, mu_max_iter=0) -> Params:
+                mu_tol=0.0, mu_max_iter=0, scf_keep_k0=0) -> Params:
     """Params from a workload.ModelParams-like object."""
     p = Params()
     p.n_atoms = int(n_atoms)
@@ -113,6 +117,7 @@ def make_params(mp, n_atoms: int, cell, precision="fp64", foe_steps=0, foe_u_max
     p.foe_u_max = float(foe_u_max)
     p.mu_max_iter = int(mu_max_iter)
     p.mu_tol = float(mu_tol)
+    p.scf_keep_k0 = int(scf_keep_k0)
     return p
 
 
@@ -290,6 +295,24 @@ class Context:
                                             float(alpha), float(beta), float(gamma), int(sym),
                                             int(split)), "sxl_mixed_gemm")
         return C
+
+    def set_derived_host(self, F, Kf):
+        self._check(self.lib.sxl_set_derived_host(self.h, _host_ptr(F), _host_ptr(Kf)),
+                    "sxl_set_derived_host")
+
+    def get_derived_host(self, F, Kf):
+        self._check(self.lib.sxl_get_derived_host(self.h, _host_ptr(F), _host_ptr(Kf)),
+                    "sxl_get_derived_host")
+
+    def enable_gemm_timing(self, on=True):
+        self._check(self.lib.sxl_enable_gemm_timing(self.h, int(on)), "sxl_enable_gemm_timing")
+
+    def timers(self, reset=False):
+        out = np.zeros(10)
+        self._check(self.lib.sxl_timers(self.h, out.ctypes.data_as(_p), int(reset)), "sxl_timers")
+        keys = ("steps", "density_ms", "forces_ms", "krylov_ms", "ranks", "tc_launches",
+                "tc_ms", "tc_mma_flops", "tc_alg_flops", "tc_fp32_flops")
+        return dict(zip(keys, out.tolist()))
 
     def info(self):
         out = np.zeros(7)

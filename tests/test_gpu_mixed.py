@@ -72,7 +72,7 @@ def dens128():
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 def test_mixed_density_and_response(sxl, dens128, prec):
     w, d = dens128
-    ctx = sxl.Context(w.params, w.n_atoms, w.cell, prec, mu_tol=1e-7)
+    ctx = sxl.Context(w.params, w.n_atoms, w.cell, prec)
     q, mu = ctx.density(w.R, w.n0)
     q = q.cpu().numpy()
     err_q = np.abs(q - d.q).max()
