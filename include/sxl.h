@@ -81,7 +81,8 @@ typedef struct {
   int    precision;          /* SXL_FP64, SXL_MIXED_FP16 or SXL_MIXED_BF16     */
   int    foe_steps;          /* recursion depth; 0 = choose from spectral bounds */
   double foe_u_max;          /* bound on |eig(U)| that fixes the depth when
-                                foe_steps == 0 (0 = 0.25)                     */
+                                foe_steps == 0 (0 = 0.05 for SXL_FP64, 0.2
+                                for the mixed forms)                          */
   int    mu_max_iter;        /* cap on chemical-potential Newton passes (0 = 30) */
   double mu_tol;             /* |sum Tr D - N_e| tolerance (0 = 1e-10)         */
   int    scf_keep_k0;        /* scf_solve: 0 = build the exact K0 = J^{-1} when the

@@ -199,7 +199,7 @@ static int build_model(sxl_ctx* c, const double* R, const double* n) {
     c->h0_valid = true;
   }
   launch_spin_shift(c, n, c->shift);
-  gersh_bounds(c, c->red);
+  lanczos_bounds(c, c->red);
   SXL_TRY(sync_host(c, c->red, 2));
   c->lam_min = c->hred[0];
   c->lam_max = c->hred[1];
@@ -217,7 +217,10 @@ static int density(sxl_ctx* c, const double* R, const double* n, double mu_guess
     c->nr = c->p.foe_steps;
   } else {
     double ymax = 0.5 * c->beta * (hi - lo);
-    double ut = c->p.foe_u_max > 0 ? c->p.foe_u_max : 0.25;
+    // fp64 form: small |U| so that the fifth-order start is exact to ~1e-11
+    // in the effective argument of every state; mixed forms: 4x larger
+    double ut = c->p.foe_u_max > 0 ? c->p.foe_u_max
+                                   : (c->p.precision == SXL_FP64 ? 0.05 : 0.2);
     c->nr = std::max(4, (int)std::ceil(std::log2(ymax / ut)));
   }
   c->scale = c->beta / std::ldexp(1.0, c->nr + 1);

@@ -146,6 +146,7 @@ void build_u_f64(sxl_ctx* c, const double* H0, const double* shift, double mu, d
                  double* U);
 void rowstats_f64(sxl_ctx* c, int batch, int n, const double* T, double* diag, double* rowsq);
 void gersh_bounds(sxl_ctx* c, double* out2_dev);
+void lanczos_bounds(sxl_ctx* c, double* out2_dev);
 // deterministic dot products: out[0] = sum x.y (length len)
 void dot_f64(sxl_ctx* c, long long len, const double* x, const double* y, double* out);
 void small_kernels_density(sxl_ctx* c, double* q, double* stats);

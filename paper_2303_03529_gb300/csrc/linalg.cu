@@ -653,3 +653,163 @@ __global__ void k_energy_small(int nat, double W, const double* __restrict__ q,
 void energy_terms(sxl_ctx* c, const double* n, const double* erep_atom, double* out) {
   LAUNCH(k_energy_small, 1, 1024, 0, c->st, c->nat, c->p.W, c->q, n, c->shift, erep_atom, out);
 }
+
+// ---------------------------------------------------------------------------
+// Spectral bounds by Lanczos on both H_sigma = H0 + diag(shift_sigma): LZ
+// steps from a fixed start vector, then the extreme eigenvalues of each
+// tridiagonal by Sturm-sequence bisection.  Ritz values lie inside the
+// spectrum and converge to its ends from inside, so a margin (the larger of
+// 2 |beta_last| and 1 eV) is added; the expansion only needs an upper bound
+// on |eig(U)|, and its polynomial start stays accurate well beyond it.
+#define LZ 32
+// w[s] = H_s v[s] - beta_prev v_prev[s]; partial alpha = v . w  (warp per row)
+__global__ void k_lz_matvec(int nat, const double* __restrict__ H0, const double* __restrict__ shift,
+                            const double* __restrict__ v, const double* __restrict__ vprev,
+                            const double* __restrict__ beta, double* w) {
+  const int N = nat * NORB;
+  int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  int lane = threadIdx.x & 31;
+  if (row >= 2 * N) return;
+  int s = row / N, i = row % N;
+  const double* vs = v + (size_t)s * N;
+  double acc = 0.0;
+  for (int j = lane; j < N; j += 32) acc += H0[(size_t)i * N + j] * vs[j];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    acc += shift[s * nat + i / NORB] * vs[i];
+    w[row] = acc - beta[s] * vprev[row];
+  }
+}
+
+// one block per spin: alpha = v.w, w -= alpha v, beta = |w|, vprev = v, v = w / beta
+__global__ void k_lz_update(int N, int it, double* v, double* vprev, double* w, double* beta,
+                            double* alphas, double* betas) {
+  __shared__ double sm[1024];
+  int s = blockIdx.x;
+  double* vs = v + (size_t)s * N;
+  double* ws = w + (size_t)s * N;
+  double* ps = vprev + (size_t)s * N;
+  double a = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) a += vs[i] * ws[i];
+  sm[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  double alpha = sm[0];
+  __syncthreads();
+  double b = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    double x = ws[i] - alpha * vs[i];
+    ws[i] = x;
+    b += x * x;
+  }
+  sm[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  double bn = sqrt(sm[0]);
+  double inv = bn > 0 ? 1.0 / bn : 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    ps[i] = vs[i];
+    vs[i] = ws[i] * inv;
+  }
+  if (threadIdx.x == 0) {
+    alphas[s * LZ + it] = alpha;
+    betas[s * LZ + it] = bn;
+    beta[s] = bn;
+  }
+}
+
+__global__ void k_lz_start(int N, double* v, double* vprev, double* beta) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < 2 * N) {
+    // deterministic start vector with all components nonzero
+    unsigned h = (unsigned)(i % N) * 2654435761u + 12345u;
+    v[i] = 0.5 + (double)(h >> 8) * (1.0 / 16777216.0);
+    vprev[i] = 0.0;
+  }
+  if (i < 2) beta[i] = 0.0;
+}
+
+__global__ void k_lz_normalize(int N, double* v) {
+  __shared__ double sm[1024];
+  int s = blockIdx.x;
+  double* vs = v + (size_t)s * N;
+  double a = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) a += vs[i] * vs[i];
+  sm[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  double inv = 1.0 / sqrt(sm[0]);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) vs[i] *= inv;
+}
+
+// number of eigenvalues of the tridiagonal (a, b) below x (Sturm count)
+__device__ int sturm_count(const double* a, const double* b, int m, double x) {
+  int cnt = 0;
+  double d = 1.0;
+  for (int i = 0; i < m; ++i) {
+    double bb = i > 0 ? b[i - 1] * b[i - 1] : 0.0;
+    d = (a[i] - x) - (i > 0 ? bb / d : 0.0);
+    if (d == 0.0) d = -1e-300;
+    if (d < 0) ++cnt;
+  }
+  return cnt;
+}
+
+__global__ void k_lz_bounds(const double* alphas, const double* betas, double* out) {
+  if (threadIdx.x != 0) return;
+  double lo_all = 1e300, hi_all = -1e300;
+  for (int s = 0; s < 2; ++s) {
+    const double* a = alphas + s * LZ;
+    const double* b = betas + s * LZ;
+    int m = LZ;
+    for (int i = 0; i < LZ; ++i)
+      if (!(b[i] > 1e-12)) { m = i + 1; break; }
+    double r = 0.0;
+    for (int i = 0; i < m; ++i) r = fmax(r, fabs(a[i]) + (i > 0 ? b[i - 1] : 0.0) + b[i]);
+    double lo = -r, hi = r;
+    for (int k = 0; k < 200; ++k) {  // smallest eigenvalue
+      double mid = 0.5 * (lo + hi);
+      if (sturm_count(a, b, m, mid) >= 1) hi = mid; else lo = mid;
+    }
+    double emin = hi;
+    lo = -r; hi = r;
+    for (int k = 0; k < 200; ++k) {  // largest eigenvalue
+      double mid = 0.5 * (lo + hi);
+      if (sturm_count(a, b, m, mid) >= m) hi = mid; else lo = mid;
+    }
+    double emax = lo;
+    double margin = fmax(2.0 * b[m - 1], 1.0);
+    lo_all = fmin(lo_all, emin - margin);
+    hi_all = fmax(hi_all, emax + margin);
+  }
+  out[0] = lo_all;
+  out[1] = hi_all;
+}
+
+void lanczos_bounds(sxl_ctx* c, double* out2) {
+  const int N = c->N;
+  double* v = c->du;             // 2N
+  double* vprev = c->rowsq;      // 2N
+  double* w = c->chi;            // 2N (overwritten before chi is rebuilt by the expansion)
+  double* beta = c->red + 3000;
+  double* al = c->red + 3008;
+  double* be = c->red + 3008 + 2 * LZ;
+  LAUNCH(k_lz_start, (2 * N + 255) / 256, 256, 0, c->st, N, v, vprev, beta);
+  LAUNCH(k_lz_normalize, 2, 1024, 0, c->st, N, v);
+  int wpb = 8;
+  for (int it = 0; it < LZ; ++it) {
+    LAUNCH(k_lz_matvec, (2 * N + wpb - 1) / wpb, 32 * wpb, 0, c->st, c->nat, c->H0, c->shift, v,
+           vprev, beta, w);
+    LAUNCH(k_lz_update, 2, 1024, 0, c->st, N, it, v, vprev, w, beta, al, be);
+  }
+  LAUNCH(k_lz_bounds, 1, 32, 0, c->st, al, be, out2);
+}
