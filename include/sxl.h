@@ -188,6 +188,27 @@ int scf_solve(sxl_ctx* ctx, const double* R_dev, double* n_dev, double tol,
 int sxl_mixed_gemm(sxl_ctx* ctx, const double* A_dev, const double* B_dev, const double* E_dev,
                    double* C_dev, double alpha, double beta, double gamma, int sym, int split);
 
+/* Allocation-free form of sxl_mixed_gemm, for callers that cannot call
+ * cudaMalloc (for example code whose device memory is all handed out by its
+ * own pool allocator, or a process that has already reserved the device's
+ * memory).  The paper has no counterpart; it is a library service.
+ *
+ * Same product and arguments as sxl_mixed_gemm, without a context: n is the
+ * matrix size (a multiple of 64, at most 576), precision SXL_MIXED_FP16 or
+ * SXL_MIXED_BF16, stream a cudaStream_t (NULL = legacy default stream).  The
+ * caller owns A, B, E (may be NULL) and C (2 x n x n fp64 each, device).
+ * Working storage lives in fixed device arrays of the library (about
+ * 10.6 MB per GPU that loads it, kept until exit); no call allocates or
+ * frees memory.  The first call on a device does a one-time set-up on the
+ * current device (symbol addresses, kernel attributes); make it before any
+ * stream capture.  All calls share the arrays: calls that overlap on the
+ * GPU race and must be serialized by the caller.  Synchronizes `stream`.
+ * Returns SXL_E_ARG for sizes beyond the maximum or a bad precision,
+ * SXL_E_CUDA if a CUDA call fails or the GEMM reports a wait timeout. */
+int sxl_mixed_gemm_noalloc(int n, int precision, const double* A_dev, const double* B_dev,
+                           const double* E_dev, double* C_dev, double alpha, double beta,
+                           double gamma, int sym, int split, void* stream);
+
 /* Device-time counters (CUDA events on the context stream) accumulated over
  * xlbomd_step calls: out[0] steps, [1] density ms, [2] forces ms, [3] Krylov
  * ms, [4] Krylov ranks, [5] tensor-core GEMM launches timed, [6] their total

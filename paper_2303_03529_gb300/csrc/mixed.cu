@@ -772,3 +772,139 @@ int mixed_gemm_test(sxl_ctx* c, const double* A, const double* B, const double* 
   DISPATCH(c, k_join_f64, g, 256, 0, nn, c->hG1.hi, c->hG1.lo, C);
   return SXL_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of sxl_mixed_gemm (no counterpart in the paper).
+//
+// Some callers cannot call cudaMalloc: code that hands all device memory to
+// its own pool allocator and must not fragment or exceed it, or a process
+// that has already reserved the device's memory.  This variant keeps its
+// working storage (the (hi, lo) 16-bit copies of A, B, E and C, and an error
+// flag) in file-scope device arrays, so it allocates nothing.  The arrays
+// are sized for matrices of at most SXL_NOALLOC_MAX_N; every GPU that loads
+// the library holds them (about 10.6 MB) until the process exits.  All
+// calls share them, so calls that overlap on the GPU (other streams, other
+// host threads) race; the error flag is cleared at the start of each call,
+// and every other element a call reads is written earlier in the same call.
+#define SXL_NOALLOC_MAX_N 576
+#define NOALLOC_MAT ((size_t)2 * SXL_NOALLOC_MAX_N * SXL_NOALLOC_MAX_N)
+static __device__ __align__(256) uint16_t g_noalloc_scratch[8 * NOALLOC_MAT];
+static __device__ __align__(256) int g_noalloc_err;
+
+#define NOALLOC_MAX_DEV 64
+static bool g_noalloc_ready[NOALLOC_MAX_DEV];
+static uint16_t* g_noalloc_ptr[NOALLOC_MAX_DEV];
+static int* g_noalloc_err_ptr[NOALLOC_MAX_DEV];
+
+template <bool BF16, bool SPLIT>
+static cudaError_t noalloc_attr() {
+  return cudaFuncSetAttribute(k_tc_gemm<BF16, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)TcCfg<SPLIT>::SMEM);
+}
+
+// One-time set-up per device, run with that device current: the device
+// addresses of the file-scope arrays (in host code their names are only
+// host-side stand-ins) and the shared-memory opt-in of the GEMM kernels.
+static int noalloc_setup(int dev) {
+  if (g_noalloc_ready[dev]) return SXL_OK;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SXL_E_CUDA;
+  void* e = nullptr;
+  if (cudaGetSymbolAddress(&e, g_noalloc_err) != cudaSuccess || !e) return SXL_E_CUDA;
+  if (noalloc_attr<false, false>() != cudaSuccess || noalloc_attr<false, true>() != cudaSuccess ||
+      noalloc_attr<true, false>() != cudaSuccess || noalloc_attr<true, true>() != cudaSuccess)
+    return SXL_E_CUDA;
+  if (!g_encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return SXL_E_UNSUPPORTED;
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  g_noalloc_ptr[dev] = (uint16_t*)p;
+  g_noalloc_err_ptr[dev] = (int*)e;
+  g_noalloc_ready[dev] = true;
+  return SXL_OK;
+}
+
+static int noalloc_map(CUtensorMap* m, const uint16_t* base, int n, int box_rows, bool bf16) {
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)(2 * (size_t)n)};
+  cuuint64_t strides[1] = {(cuuint64_t)n * 2};
+  cuuint32_t box[2] = {TC_BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                        2, (void*)base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? SXL_OK : SXL_E_CUDA;
+}
+
+template <bool BF16>
+static int noalloc_run(int n, uint16_t* sc, int* err, const double* A, const double* B,
+                       const double* E, double* C, double alpha, double beta, double gamma,
+                       int sym, int split, cudaStream_t st) {
+  const size_t nn = 2 * (size_t)n * n;
+  uint16_t* Ah = sc;
+  uint16_t* Al = sc + NOALLOC_MAT;
+  uint16_t* Bh = sc + 2 * NOALLOC_MAT;
+  uint16_t* Bl = sc + 3 * NOALLOC_MAT;
+  uint16_t* Eh = sc + 4 * NOALLOC_MAT;
+  uint16_t* El = sc + 5 * NOALLOC_MAT;
+  uint16_t* Ch = sc + 6 * NOALLOC_MAT;
+  uint16_t* Cl = sc + 7 * NOALLOC_MAT;
+  const unsigned g = (unsigned)((nn + 255) / 256);
+  if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess) return SXL_E_CUDA;
+  k_split_f64<BF16><<<g, 256, 0, st>>>(nn, A, Ah, Al);
+  k_split_f64<BF16><<<g, 256, 0, st>>>(nn, B, Bh, Bl);
+  if (E) k_split_f64<BF16><<<g, 256, 0, st>>>(nn, E, Eh, El);
+  CUtensorMap maps[4];
+  if (noalloc_map(&maps[0], Ah, n, TC_BM, BF16) || noalloc_map(&maps[1], Al, n, TC_BM, BF16) ||
+      noalloc_map(&maps[2], Bh, n, TC_BN, BF16) || noalloc_map(&maps[3], Bl, n, TC_BN, BF16))
+    return SXL_E_CUDA;
+  TcArgs a;
+  a.n = n;
+  a.ntm = (n + TC_BM - 1) / TC_BM;
+  a.ntn = (n + TC_BN - 1) / TC_BN;
+  a.nk = n / TC_BK;
+  a.alpha = (float)alpha;
+  a.beta = (float)beta;
+  a.gamma = (float)gamma;
+  a.Ehi = E ? Eh : nullptr;
+  a.Elo = E ? El : nullptr;
+  a.Chi = Ch;
+  a.Clo = Cl;
+  a.sym = sym ? 1 : 0;
+  a.err = err;
+  dim3 grid(a.ntm * a.ntn, 2);
+  if (split)
+    k_tc_gemm<BF16, true><<<grid, 192, TcCfg<true>::SMEM, st>>>(maps[0], maps[1], maps[2], maps[3], a);
+  else
+    k_tc_gemm<BF16, false><<<grid, 192, TcCfg<false>::SMEM, st>>>(maps[0], maps[1], maps[2], maps[3], a);
+  k_join_f64<BF16><<<g, 256, 0, st>>>(nn, Ch, Cl, C);
+  if (cudaGetLastError() != cudaSuccess) return SXL_E_CUDA;
+  int flag = 0;
+  if (cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return SXL_E_CUDA;
+  return flag ? SXL_E_CUDA : SXL_OK;
+}
+
+extern "C" int sxl_mixed_gemm_noalloc(int n, int precision, const double* A, const double* B,
+                                      const double* E, double* C, double alpha, double beta,
+                                      double gamma, int sym, int split, void* stream) {
+  if (!A || !B || !C) return SXL_E_ARG;
+  if (n < 64 || n > SXL_NOALLOC_MAX_N || n % 64 != 0) return SXL_E_ARG;
+  if (precision != SXL_MIXED_FP16 && precision != SXL_MIXED_BF16) return SXL_E_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEV) return SXL_E_CUDA;
+  int r = noalloc_setup(dev);
+  if (r != SXL_OK) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (precision == SXL_MIXED_BF16)
+    return noalloc_run<true>(n, g_noalloc_ptr[dev], g_noalloc_err_ptr[dev], A, B, E, C, alpha,
+                             beta, gamma, sym, split, st);
+  return noalloc_run<false>(n, g_noalloc_ptr[dev], g_noalloc_err_ptr[dev], A, B, E, C, alpha,
+                            beta, gamma, sym, split, st);
+}

@@ -69,6 +69,7 @@ EXPORTS = {
     "sxl_get_derived_host": (_i, [_p, _p, _p]),
     "sxl_timers": (_i, [_p, _p, _i]),
     "sxl_enable_gemm_timing": (_i, [_p, _i]),
+    "sxl_mixed_gemm_noalloc": (_i, [_i, _i, _p, _p, _p, _p, _d, _d, _d, _i, _i, _p]),
 }
 
 _lib = None
@@ -319,6 +320,25 @@ class Context:
         self._check(self.lib.sxl_info(self.h, out.ctypes.data_as(_p)), "sxl_info")
         keys = ("mu", "N", "foe_steps", "lam_min", "lam_max", "gemms", "launches")
         return dict(zip(keys, out.tolist()))
+
+
+def mixed_gemm_noalloc(n, precision, A, B, E=None, alpha=1.0, beta=0.0, gamma=0.0,
+                       sym=False, split=True, stream=None):
+    """Allocation-free tensor-core product (sxl_mixed_gemm_noalloc): the caller
+    passes A, B, E and receives C (2 x n x n fp64 CUDA tensors)."""
+    import torch
+    lib = load_library()
+    nn = 2 * n * n
+    C = torch.empty(2, n, n, dtype=torch.float64, device="cuda")
+    st = stream if stream is not None else torch.cuda.current_stream()
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    rc = lib.sxl_mixed_gemm_noalloc(int(n), prec, _ptr(A, nn), _ptr(B, nn),
+                                    _ptr(E, nn) if E is not None else None, _ptr(C),
+                                    float(alpha), float(beta), float(gamma), int(sym), int(split),
+                                    _p(st.cuda_stream))
+    if rc != 0:
+        raise SxlError(f"sxl_mixed_gemm_noalloc failed ({rc})")
+    return C
 
 
 def _host_ptr(a):
