@@ -145,7 +145,10 @@ int forces(sxl_ctx* ctx, const double* R_dev, const double* n_dev,
 
 /* MD state: positions, velocities, n history (kmax+1 vectors of 2 N_at,
  * newest first) and mu.  Device-pointer and host-pointer variants.  After
- * setting the state, xlbomd_step evaluates forces and Kf at it first. */
+ * setting the state, xlbomd_step evaluates forces and Kf at it first.  The
+ * chemical-potential search of each step starts from the linear
+ * extrapolation of the last two steps' mu; setting a state whose mu equals
+ * the context's current mu keeps that history, any other mu clears it. */
 int sxl_set_state(sxl_ctx* ctx, const double* R_dev, const double* V_dev,
                   const double* nhist_dev, double mu);
 int sxl_get_state(sxl_ctx* ctx, double* R_dev, double* V_dev, double* nhist_dev,

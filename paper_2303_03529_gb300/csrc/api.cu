@@ -220,7 +220,7 @@ static int density(sxl_ctx* c, const double* R, const double* n, double mu_guess
     // fp64 form: small |U| so that the fifth-order start is exact to ~1e-11
     // in the effective argument of every state; mixed forms: 4x larger
     double ut = c->p.foe_u_max > 0 ? c->p.foe_u_max
-                                   : (c->p.precision == SXL_FP64 ? 0.05 : 0.2);
+                                   : (c->p.precision == SXL_FP64 ? 0.05 : 0.25);
     c->nr = std::max(4, (int)std::ceil(std::log2(ymax / ut)));
   }
   c->scale = c->beta / std::ldexp(1.0, c->nr + 1);
@@ -254,6 +254,18 @@ static int density(sxl_ctx* c, const double* R, const double* n, double mu_guess
     if (it + 1 >= maxit)
       return sxl_fail(c, SXL_E_NO_CONVERGENCE, "chemical potential search hit its iteration cap");
     if (err > 0) hi = mu; else lo = mu;
+    // mixed forms: a small remaining shift is applied to first order (one
+    // product instead of another expansion pass)
+    if (mixed && dN > 0 && c->beta * std::fabs(err / dN) <= 3e-3) {
+      double dmu = -err / dN;
+      SXL_TRY(mu_shift_mixed(c, dmu, stats));
+      SXL_TRY(sync_host(c, stats, 2));
+      mu += dmu;
+      c->last_N = c->hred[0];
+      if (dbg)
+        fprintf(stderr, "[sxl] mu first-order shift %.3e -> N %.10f\n", dmu, c->hred[0]);
+      break;
+    }
     double mn = (dN > 0) ? mu - err / dN : 0.5 * (lo + hi);
     if (!(mn > lo && mn < hi)) mn = 0.5 * (lo + hi);
     mu = mn;
@@ -345,6 +357,38 @@ __global__ void k_energy_band(int N, const double* __restrict__ H0, double d0s, 
   if (threadIdx.x == 0) out[0] = 0.5 * (ttr - dots[0]) + 0.5 * (ttr - dots[1]) - 2.0 * sm[0];
 }
 
+__global__ void k_entropy_combine_f64(int N, int nr, const double* ld, const double* dots,
+                                      double* out) {
+  if (threadIdx.x != 0) return;
+  double tot = 0.0;
+  for (int s = 0; s < 2; ++s) {
+    double v = -N * 0.69314718055994531 + ldexp(1.0, nr - 1) * ld[s] + ldexp(1.0, nr) * dots[s];
+    for (int k = 0; k < nr; ++k) v += ldexp(1.0, nr - 1 - k) * ld[2 * (k + 1) + s];
+    tot += v;
+  }
+  out[0] = tot;
+}
+
+// sum over spins and states of f ln f + (1 - f) ln(1 - f) (see chol.cu)
+static int entropy_f64(sxl_ctx* c, double* out_dev) {
+  const int N = c->N, nr = c->nr;
+  const size_t nn = (size_t)N * N;
+  double* ld = c->red + 3200;
+  double* dots = c->red + 3190;
+  CUDA_TRY(c, cudaMemsetAsync(ld, 0, 2 * (nr + 1) * sizeof(double), c->st));
+  gemm_f64(c, 2, N, c->T[0], c->T[0], c->X0, -1.0, nullptr, 0.0, 1.0, true);  // I - T_0^2
+  chol_logdet_f64(c, N, c->X0, ld);
+  for (int k = 0; k < nr; ++k) {
+    CUDA_TRY(c, cudaMemcpyAsync(c->X0, c->Y[k], 2 * nn * sizeof(double), cudaMemcpyDeviceToDevice,
+                                c->st));
+    chol_logdet_f64(c, N, c->X0, ld + 2 * (k + 1));
+  }
+  dot_f64(c, (long long)nn, c->U, c->T[nr], dots);
+  dot_f64(c, (long long)nn, c->U + nn, c->T[nr] + nn, dots + 1);
+  LAUNCH(k_entropy_combine_f64, 1, 32, 0, c->st, N, nr, ld, dots, out_dev);
+  return SXL_OK;
+}
+
 // forces at the current density; energies (6 doubles, host) if requested
 static int eval_forces(sxl_ctx* c, const double* R, const double* n, double* F, double* en) {
   double* erep = c->tmpv;  // nat doubles
@@ -362,9 +406,11 @@ static int eval_forces(sxl_ctx* c, const double* R, const double* n, double* F, 
     LAUNCH(k_energy_band, 1, 1024, 0, c->st, c->N, c->H0, c->p.d0_s, c->p.d0_p, c->p.d0_d, d,
            d + 2);
     energy_terms(c, n, erep, d + 3);
-    SXL_TRY(sync_host(c, d + 2, 4));
+    if (c->p.precision != SXL_FP64) SXL_TRY(entropy_mixed(c, d + 6));
+    else SXL_TRY(entropy_f64(c, d + 6));
+    SXL_TRY(sync_host(c, d + 2, 5));
     double band = c->hred[0], coul = c->hred[1], spin = c->hred[2], rep = c->hred[3];
-    double ent = 0.0;  // entropy: see sxl_energy_entropy
+    double ent = c->p.kT * c->hred[4];
     en[0] = band + coul + spin + ent + rep;
     en[1] = band; en[2] = coul; en[3] = spin; en[4] = ent; en[5] = rep;
   }
@@ -399,6 +445,9 @@ int sxl_create(const sxl_params* prm, void* stream, sxl_ctx** out) {
   c->beta = 1.0 / p.kT;
   c->hist_head = 0;
   c->mu = NAN;
+  c->mu_prev = NAN;
+  c->teff_valid = false;
+  c->fscratch = nullptr;
   c->state_ready = c->evaluated = c->have_density = c->h0_valid = false;
   c->nr = 0; c->nr_cap = 0;
   c->lam_min = 0; c->lam_max = 0;
@@ -586,6 +635,9 @@ static int set_state(sxl_ctx* c, const double* R, const double* V, const double*
   CUDA_TRY(c, cudaMemcpyAsync(c->nhist, nh, (size_t)K1 * n2 * sizeof(double), kind, c->st));
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   c->hist_head = 0;
+  // the same mu as the context holds continues its trajectory: keep the mu
+  // history used to extrapolate the next start; any other mu starts afresh
+  if (!(mu == c->mu)) c->mu_prev = NAN;
   c->mu = mu;
   c->state_ready = true;
   c->evaluated = false;
@@ -628,7 +680,12 @@ static int evaluate(sxl_ctx* c, double* en) {
   c->have_density = false;
   // each phase gets its own start/end event pair (events are recycled per pair)
   cudaEvent_t d0 = phase_mark(c);
-  SXL_TRY(density(c, c->R, n, c->mu));
+  // linear extrapolation of mu along the trajectory as the Newton start
+  double guess = c->mu;
+  if (std::isfinite(c->mu) && std::isfinite(c->mu_prev)) guess = 2.0 * c->mu - c->mu_prev;
+  double mu_old = c->mu;
+  SXL_TRY(density(c, c->R, n, guess));
+  c->mu_prev = mu_old;
   cudaEvent_t d1 = phase_mark(c), f0 = phase_mark(c);
   SXL_TRY(eval_forces(c, c->R, n, c->F, en));
   cudaEvent_t f1 = phase_mark(c), k0 = phase_mark(c);

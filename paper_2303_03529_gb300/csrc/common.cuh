@@ -65,6 +65,10 @@ struct sxl_ctx {
   // mixed-precision chain
   MatH hU, hS, hQ, hX0, hX1, hP, hSm, hdTa, hdTb, hG1;
   std::vector<MatH> hT, hY;
+  MatH hTeff;             // T_nr after a first-order chemical-potential shift
+  float* fscratch;        // 2 N^2 fp32 (entropy factorizations, mixed forms)
+  bool teff_valid;        // hTeff (not hT[nr]) holds the final density
+  double mu_prev;         // chemical potential of the previous MD step (NaN: none)
 
   double *diagT, *rowsq, *chi;  // 2N each
   double *du;                   // 2N perturbation (scaled) per orbital
@@ -90,6 +94,12 @@ struct sxl_ctx {
   double tc_launches, tc_ms, tc_mma_flops, tc_alg_flops, tc_f32_flops;
   std::vector<EvPair> ph_pending;    // phase events: mma_flops = phase id
 };
+
+// Cholesky log-determinants of two SPD matrices (chol.cu); A is destroyed
+void chol_logdet_f64(sxl_ctx* c, int n, double* A, double* logdet);
+void chol_logdet_f32(sxl_ctx* c, int n, float* A, double* logdet);
+void chol_logdet_dev_f32(sxl_ctx* c, int n, float* W, double* logdet);
+int entropy_mixed(sxl_ctx* c, double* out_dev);
 
 // event helpers (api.cu)
 cudaEvent_t ev_get(sxl_ctx* c);
@@ -170,6 +180,8 @@ void energy_terms(sxl_ctx* c, const double* n, const double* erep_atom, double* 
 int sxl_mixed_supported(sxl_ctx* c);
 void sxl_mixed_free(sxl_ctx* c);
 int foe_mixed(sxl_ctx* c, double mu, double* stats_dev);
+int mu_shift_mixed(sxl_ctx* c, double dmu, double* stats_dev);
+const MatH& final_T_mixed(const sxl_ctx* c);
 int dmpt_mixed(sxl_ctx* c, const double* du);
 void dot_h0_t_mixed(sxl_ctx* c, int spin, double* out);
 void density_matrix_mixed(sxl_ctx* c, double* D);

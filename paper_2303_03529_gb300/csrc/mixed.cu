@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #define TC_BM 128
 #define TC_BN 256
@@ -123,15 +124,20 @@ __device__ __forceinline__ void tmem_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes (64 16-bit elements), 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+// Shared-memory matrix descriptor of a K-major operand whose rows are BK
+// 16-bit elements (BK = 64: 128-byte rows, 128-byte swizzle, 8-row groups
+// 1024 bytes apart; BK = 32: 64-byte rows, 64-byte swizzle, groups 512 bytes
+// apart).  The leading byte offset is unused for these layouts.
+template <int BK>
+__device__ __forceinline__ uint64_t sdesc_kmajor(uint32_t saddr) {
+  constexpr uint32_t row_bytes = BK * 2;
+  constexpr uint64_t layout = (BK == 64) ? 2 : 4;  // SWIZZLE_128B : SWIZZLE_64B
   uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
-  d |= (uint64_t)1 << 16;                    // leading byte offset (unused here) = 16 B
-  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset = 1024 B
-  d |= (uint64_t)1 << 46;                    // descriptor version
-  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);        // start address
+  d |= (uint64_t)1 << 16;                          // leading byte offset = 16 B
+  d |= (uint64_t)((8 * row_bytes) >> 4) << 32;     // stride byte offset
+  d |= (uint64_t)1 << 46;                          // descriptor version
+  d |= layout << 61;
   return d;
 }
 // Instruction descriptor, kind::f16: fp32 accumulator, A/B fp16 (0) or bf16 (1),
@@ -169,11 +175,13 @@ template <bool BF16>
 __device__ __forceinline__ double ld_hl_d(const uint16_t* hi, const uint16_t* lo, size_t i) {
   return (double)HL<BF16>::f(hi[i]) + (double)HL<BF16>::f(lo[i]) * (double)LO_INV;
 }
+// store v as (hi, lo): both parts carry at most 22 significant bits together,
+// so fp32 (24 bits) is exact enough for the split
 template <bool BF16>
-__device__ __forceinline__ void st_hl(uint16_t* hi, uint16_t* lo, size_t i, double v) {
-  uint16_t h = HL<BF16>::b((float)v);
+__device__ __forceinline__ void st_hl(uint16_t* hi, uint16_t* lo, size_t i, float v) {
+  uint16_t h = HL<BF16>::b(v);
   hi[i] = h;
-  lo[i] = HL<BF16>::b((float)((v - (double)HL<BF16>::f(h)) * (double)LO_SCALE));
+  lo[i] = HL<BF16>::b((v - HL<BF16>::f(h)) * LO_SCALE);
 }
 
 // ---------------------------------------------------------------------------
@@ -188,22 +196,22 @@ struct TcArgs {
   int* err;
 };
 
-template <bool SPLIT>
+template <bool SPLIT, int BK>
 struct TcCfg {
-  static constexpr int STAGES = SPLIT ? 2 : 4;
-  static constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2;
-  static constexpr uint32_t B_BYTES = TC_BN * TC_BK * 2;
+  static constexpr uint32_t A_BYTES = TC_BM * BK * 2;
+  static constexpr uint32_t B_BYTES = TC_BN * BK * 2;
   static constexpr uint32_t STAGE_BYTES = (A_BYTES + B_BYTES) * (SPLIT ? 2 : 1);
+  static constexpr int STAGES = (int)((196608u / STAGE_BYTES) > 8 ? 8 : (196608u / STAGE_BYTES));
   static constexpr uint32_t TMEM_COLS = SPLIT ? 512 : 256;
   static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
 };
 
-template <bool BF16, bool SPLIT>
+template <bool BF16, bool SPLIT, int BK = TC_BK>
 __global__ void __launch_bounds__(192, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
               TcArgs g) {
-  using Cfg = TcCfg<SPLIT>;
+  using Cfg = TcCfg<SPLIT, BK>;
   constexpr int STAGES = Cfg::STAGES;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_bar;
@@ -263,7 +271,7 @@ __global__ void __launch_bounds__(192, 1)
         const uint32_t fb = smem_u32(&full_bar[s]);
         mbar_expect_tx(fb, Cfg::STAGE_BYTES);
         const uint32_t st = sbase + s * Cfg::STAGE_BYTES;
-        const int kx = kb * TC_BK;
+        const int kx = kb * BK;
         tma_load_2d(st, &mAh, fb, kx, bz * g.n + row0);
         tma_load_2d(st + Cfg::A_BYTES, &mBh, fb, kx, bz * g.n + col0);
         if (SPLIT) {
@@ -283,12 +291,12 @@ __global__ void __launch_bounds__(192, 1)
         if (!mbar_wait(smem_u32(&full_bar[s]), ph, &s_abort, true)) break;
         tc_fence_after();
         const uint32_t st = sbase + s * Cfg::STAGE_BYTES;
-        const uint64_t dAh = sdesc_sw128(st);
-        const uint64_t dBh = sdesc_sw128(st + Cfg::A_BYTES);
-        const uint64_t dAl = sdesc_sw128(st + Cfg::A_BYTES + Cfg::B_BYTES);
-        const uint64_t dBl = sdesc_sw128(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES);
+        const uint64_t dAh = sdesc_kmajor<BK>(st);
+        const uint64_t dBh = sdesc_kmajor<BK>(st + Cfg::A_BYTES);
+        const uint64_t dAl = sdesc_kmajor<BK>(st + Cfg::A_BYTES + Cfg::B_BYTES);
+        const uint64_t dBl = sdesc_kmajor<BK>(st + 2 * Cfg::A_BYTES + Cfg::B_BYTES);
 #pragma unroll
-        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+        for (int kk = 0; kk < BK / 16; ++kk) {
           const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
           const uint64_t adv = (uint64_t)(2 * kk);  // 16 elements = 32 bytes = 2 units
           umma_f16(tmem, dAh + adv, dBh + adv, idesc, acc);
@@ -303,6 +311,8 @@ __global__ void __launch_bounds__(192, 1)
       umma_commit(smem_u32(&acc_bar));
     }
   } else {
+    // Epilogue in fp32: acc0 + acc1 2^-12 keeps 24 bits, and w - rn(w) of the
+    // hi/lo split is exact in fp32, so no fp64 arithmetic is needed here.
     const int q = warp & 3;  // TMEM lane quarter this warp may access
     const int row = row0 + q * 32 + lane;
     bool ok = mbar_wait(smem_u32(&acc_bar), 0, &s_abort, true);
@@ -316,20 +326,66 @@ __global__ void __launch_bounds__(192, 1)
         tmem_ld32(ta, a0);
         if (SPLIT) tmem_ld32(ta + 256, a1);
         tmem_wait_ld();
-        if (row < g.n) {
-          const size_t rb = mat + (size_t)row * g.n;
-#pragma unroll 4
+        const int c0 = col0 + cc;
+        if (row >= g.n || c0 >= g.n) continue;  // n % 64 == 0: a chunk is all in or all out
+        const size_t rb = mat + (size_t)row * g.n + c0;
+        float v[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          float x = __uint_as_float(a0[j]);
+          if (SPLIT) x = fmaf(__uint_as_float(a1[j]), LO_INV, x);
+          v[j] = g.alpha * x;
+        }
+        if (g.Ehi) {
+          const uint4* eh = reinterpret_cast<const uint4*>(g.Ehi + rb);
+          const uint4* el = reinterpret_cast<const uint4*>(g.Elo + rb);
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            uint4 h = eh[w], l = el[w];
+            const uint16_t* hh = reinterpret_cast<const uint16_t*>(&h);
+            const uint16_t* ll = reinterpret_cast<const uint16_t*>(&l);
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              v[8 * w + e] = fmaf(g.beta, fmaf(HL<BF16>::f(ll[e]), LO_INV, HL<BF16>::f(hh[e])),
+                                  v[8 * w + e]);
+          }
+        }
+        if (row >= c0 && row < c0 + 32) v[row - c0] += g.gamma;
+        uint16_t hs[32], ls[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          uint16_t h = HL<BF16>::b(v[j]);
+          hs[j] = h;
+          ls[j] = HL<BF16>::b((v[j] - HL<BF16>::f(h)) * LO_SCALE);
+        }
+        if (!g.sym || row <= c0) {
+          // whole chunk owned: 16-byte stores along the row
+          uint4* oh = reinterpret_cast<uint4*>(g.Chi + rb);
+          uint4* ol = reinterpret_cast<uint4*>(g.Clo + rb);
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            oh[w] = *reinterpret_cast<const uint4*>(&hs[8 * w]);
+            ol[w] = *reinterpret_cast<const uint4*>(&ls[8 * w]);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (row <= c0 + j) {
+              g.Chi[rb + j] = hs[j];
+              g.Clo[rb + j] = ls[j];
+            }
+        }
+        if (g.sym) {
+          // mirrored element (c, row) for row < c: lanes hold consecutive rows,
+          // so each j writes 32 consecutive elements of row c
+#pragma unroll
           for (int j = 0; j < 32; ++j) {
-            const int col = col0 + cc + j;
-            if (col >= g.n) break;
-            if (g.sym && row > col) continue;
-            float v = __uint_as_float(a0[j]);
-            if (SPLIT) v += __uint_as_float(a1[j]) * LO_INV;
-            double w = (double)g.alpha * (double)v;
-            if (g.Ehi) w += (double)g.beta * ld_hl_d<BF16>(g.Ehi, g.Elo, rb + col);
-            if (row == col) w += (double)g.gamma;
-            st_hl<BF16>(g.Chi, g.Clo, rb + col, w);
-            if (g.sym && row != col) st_hl<BF16>(g.Chi, g.Clo, mat + (size_t)col * g.n + row, w);
+            const int col = c0 + j;
+            if (row < col) {
+              const size_t mi = mat + (size_t)col * g.n + row;
+              g.Chi[mi] = hs[j];
+              g.Clo[mi] = ls[j];
+            }
           }
         }
       }
@@ -374,25 +430,25 @@ static int get_encode(sxl_ctx* c) {
 }
 
 static int make_map(sxl_ctx* c, CUtensorMap* m, const uint16_t* base, int n, int box_rows,
-                    bool bf16) {
+                    bool bf16, int bk = TC_BK) {
   cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)(2 * (size_t)n)};
   cuuint64_t strides[1] = {(cuuint64_t)n * 2};
-  cuuint32_t box[2] = {TC_BK, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = g_encode(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
                         2, (void*)base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                        bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return sxl_fail(c, SXL_E_CUDA, "cuTensorMapEncodeTiled failed");
   return SXL_OK;
 }
 
-template <bool BF16, bool SPLIT>
+template <bool BF16, bool SPLIT, int BK>
 static int launch_tc(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a) {
-  using Cfg = TcCfg<SPLIT>;
+  using Cfg = TcCfg<SPLIT, BK>;
   static bool attr = false;
   if (!attr) {
-    CUDA_TRY(c, cudaFuncSetAttribute(k_tc_gemm<BF16, SPLIT>,
+    CUDA_TRY(c, cudaFuncSetAttribute(k_tc_gemm<BF16, SPLIT, BK>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
     attr = true;
   }
@@ -403,7 +459,7 @@ static int launch_tc(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a) {
     e1 = ev_get(c);
     CUDA_TRY(c, cudaEventRecord(e0, c->st));
   }
-  k_tc_gemm<BF16, SPLIT><<<grid, 192, Cfg::SMEM, c->st>>>(maps[0], maps[1], maps[2], maps[3], a);
+  k_tc_gemm<BF16, SPLIT, BK><<<grid, 192, Cfg::SMEM, c->st>>>(maps[0], maps[1], maps[2], maps[3], a);
   ++g_sxl_launches;
   if (c->time_tc) {
     CUDA_TRY(c, cudaEventRecord(e1, c->st));
@@ -427,16 +483,25 @@ int gemm_tc(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C, float alpha
             const MatH* E, float beta, float gamma, bool sym, bool split) {
   const bool bf16 = c->p.precision == SXL_MIXED_BF16;
   const int n = c->N;
+  // K-block per product form (measured at n = 9216): split products run best
+  // with 32-wide blocks (four 48 KB stages), plain ones with 64-wide blocks
+  // (four 48 KB stages as well).  SXL_TC_BK=32 or 64 forces one width.
+  static int bk_env = -1;
+  if (bk_env < 0) {
+    const char* e = getenv("SXL_TC_BK");
+    bk_env = e ? atoi(e) : 0;
+  }
+  const int bk = (bk_env == 32 || bk_env == 64) ? bk_env : (split ? 32 : 64);
   CUtensorMap maps[4];
-  SXL_TRY(make_map(c, &maps[0], A.hi, n, TC_BM, bf16));
-  SXL_TRY(make_map(c, &maps[1], A.lo, n, TC_BM, bf16));
-  SXL_TRY(make_map(c, &maps[2], B.hi, n, TC_BN, bf16));
-  SXL_TRY(make_map(c, &maps[3], B.lo, n, TC_BN, bf16));
+  SXL_TRY(make_map(c, &maps[0], A.hi, n, TC_BM, bf16, bk));
+  SXL_TRY(make_map(c, &maps[1], A.lo, n, TC_BM, bf16, bk));
+  SXL_TRY(make_map(c, &maps[2], B.hi, n, TC_BN, bf16, bk));
+  SXL_TRY(make_map(c, &maps[3], B.lo, n, TC_BN, bf16, bk));
   TcArgs a;
   a.n = n;
   a.ntm = (n + TC_BM - 1) / TC_BM;
   a.ntn = (n + TC_BN - 1) / TC_BN;
-  a.nk = n / TC_BK;
+  a.nk = n / bk;
   a.alpha = alpha;
   a.beta = beta;
   a.gamma = gamma;
@@ -447,8 +512,12 @@ int gemm_tc(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C, float alpha
   a.sym = sym ? 1 : 0;
   a.err = g_tc_err;
   c->n_gemm++;
-  if (bf16) return split ? launch_tc<true, true>(c, maps, a) : launch_tc<true, false>(c, maps, a);
-  return split ? launch_tc<false, true>(c, maps, a) : launch_tc<false, false>(c, maps, a);
+  if (bk == 64) {
+    if (bf16) return split ? launch_tc<true, true, 64>(c, maps, a) : launch_tc<true, false, 64>(c, maps, a);
+    return split ? launch_tc<false, true, 64>(c, maps, a) : launch_tc<false, false, 64>(c, maps, a);
+  }
+  if (bf16) return split ? launch_tc<true, true, 32>(c, maps, a) : launch_tc<true, false, 32>(c, maps, a);
+  return split ? launch_tc<false, true, 32>(c, maps, a) : launch_tc<false, false, 32>(c, maps, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -467,8 +536,8 @@ __global__ void k_build_u_h(int nat, const double* __restrict__ H0, const double
     u0 = scale * (h + shift[r / NORB] - mu);
     u1 = scale * (h + shift[nat + r / NORB] - mu);
   }
-  st_hl<BF16>(hi, lo, i, u0);
-  st_hl<BF16>(hi, lo, total + i, u1);
+  st_hl<BF16>(hi, lo, i, (float)u0);
+  st_hl<BF16>(hi, lo, total + i, (float)u1);
 }
 
 template <bool BF16>
@@ -477,8 +546,8 @@ __global__ void k_axpy_diag_h(size_t total, int n, uint16_t* ohi, uint16_t* olo,
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i >= total) return;
   size_t e = i % ((size_t)n * n);
-  double v = a * ld_hl_d<BF16>(xhi, xlo, i);
-  if (e / n == e % n) v += g;
+  float v = (float)a * ld_hl<BF16>(xhi, xlo, i);
+  if (e / n == e % n) v += (float)g;
   st_hl<BF16>(ohi, olo, i, v);
 }
 
@@ -489,25 +558,26 @@ __global__ void k_symcombo_h(int n, uint16_t* ohi, uint16_t* olo, double a, cons
                              const uint16_t* ylo, double cc, const double* w, const uint16_t* zhi,
                              const uint16_t* zlo) {
   const size_t bs = (size_t)n * n * blockIdx.z;
-  __shared__ double tile[32][33];
+  __shared__ float tile[32][33];
   int bx = blockIdx.x * 32, by = blockIdx.y * 32;
   int tx = threadIdx.x, ty = threadIdx.y;
   if (yhi) {
     for (int k = ty; k < 32; k += 8) {
       int r = bx + k, col = by + tx;
-      tile[k][tx] = (r < n && col < n) ? ld_hl_d<BF16>(yhi, ylo, bs + (size_t)r * n + col) : 0.0;
+      tile[k][tx] = (r < n && col < n) ? ld_hl<BF16>(yhi, ylo, bs + (size_t)r * n + col) : 0.f;
     }
   }
   __syncthreads();
   const double* wv = w ? w + (size_t)n * blockIdx.z : nullptr;
+  const float fa = (float)a, fb = (float)b, fc = (float)cc;
   for (int k = ty; k < 32; k += 8) {
     int r = by + k, col = bx + tx;
     if (r >= n || col >= n) continue;
     size_t idx = bs + (size_t)r * n + col;
-    double v = 0.0;
-    if (xhi) v += a * ld_hl_d<BF16>(xhi, xlo, idx);
-    if (yhi) v += b * (ld_hl_d<BF16>(yhi, ylo, idx) + tile[tx][k]);
-    if (zhi) v += cc * (wv[r] + wv[col]) * ld_hl_d<BF16>(zhi, zlo, idx);
+    float v = 0.f;
+    if (xhi) v += fa * ld_hl<BF16>(xhi, xlo, idx);
+    if (yhi) v += fb * (ld_hl<BF16>(yhi, ylo, idx) + tile[tx][k]);
+    if (zhi) v += fc * (float)(wv[r] + wv[col]) * ld_hl<BF16>(zhi, zlo, idx);
     st_hl<BF16>(ohi, olo, idx, v);
   }
 }
@@ -630,14 +700,19 @@ int sxl_mixed_supported(sxl_ctx* c) {
     CUDA_TRY(c, cudaMalloc((void**)&g_tc_err, sizeof(int)));
     CUDA_TRY(c, cudaMemset(g_tc_err, 0, sizeof(int)));
   }
-  MatH* ms[] = {&c->hU, &c->hS, &c->hQ, &c->hX0, &c->hX1, &c->hP, &c->hSm, &c->hdTa, &c->hdTb, &c->hG1};
+  MatH* ms[] = {&c->hU, &c->hS, &c->hQ, &c->hX0, &c->hX1, &c->hP, &c->hSm, &c->hdTa, &c->hdTb, &c->hG1,
+                &c->hTeff};
   for (MatH* m : ms) SXL_TRY(halloc(c, m));
+  c->teff_valid = false;
   return SXL_OK;
 }
 
 void sxl_mixed_free(sxl_ctx* c) {
-  MatH* ms[] = {&c->hU, &c->hS, &c->hQ, &c->hX0, &c->hX1, &c->hP, &c->hSm, &c->hdTa, &c->hdTb, &c->hG1};
+  MatH* ms[] = {&c->hU, &c->hS, &c->hQ, &c->hX0, &c->hX1, &c->hP, &c->hSm, &c->hdTa, &c->hdTb, &c->hG1,
+                &c->hTeff};
   for (MatH* m : ms) hfree(*m);
+  if (c->fscratch) cudaFree(c->fscratch);
+  c->fscratch = nullptr;
   for (MatH& m : c->hT) hfree(m);
   for (MatH& m : c->hY) hfree(m);
   c->hT.clear();
@@ -682,7 +757,10 @@ int foe_mixed(sxl_ctx* c, double mu, double* stats_dev) {
                   true, split));
   SXL_TRY(gemm_tc(c, c->hU, c->hQ, c->hT[0], 1.f, nullptr, 0.f, 0.f, true, split));
   double t = std::min(tanh5(c->umax), 1.0);
-  const double tol = 1e-9;
+  // the split products carry about 22 bits (fp16) or 16 bits (bf16): a
+  // Newton-Schulz error bound of 1e-7 is at that floor
+  const double tol = 1e-7;
+  c->teff_valid = false;
   c->ns_iters.assign(nr, 0);
   for (int k = 0; k < nr; ++k) {
     const MatH& Sq = c->hSm;
@@ -698,8 +776,12 @@ int foe_mixed(sxl_ctx* c, double mu, double* stats_dev) {
     axpy_diag_h(c, *cur, -ci * ci, Sq, 2.0 * ci - ci * ci);
     for (int it = 0; it < j; ++it) {
       const MatH* nxt = (it == j - 1) ? &c->hY[k] : (cur == &c->hX0 ? &c->hX1 : &c->hX0);
-      SXL_TRY(gemm_tc(c, *cur, Sq, c->hP, 1.f, cur, 1.f, 0.f, false, split));
-      SXL_TRY(gemm_tc(c, c->hP, *cur, *nxt, -1.f, cur, 2.f, 0.f, true, split));
+      // Newton-Schulz corrects its own rounding: every iteration but the last
+      // runs on the hi parts alone (one product per k step); the last one, in
+      // split form, squares the remaining error down to the split floor
+      const bool sp = split && (it == j - 1);
+      SXL_TRY(gemm_tc(c, *cur, Sq, c->hP, 1.f, cur, 1.f, 0.f, false, sp));
+      SXL_TRY(gemm_tc(c, c->hP, *cur, *nxt, -1.f, cur, 2.f, 0.f, true, sp));
       cur = nxt;
     }
     SXL_TRY(gemm_tc(c, c->hT[k], c->hY[k], c->hT[k + 1], 2.f, nullptr, 0.f, 0.f, true, split));
@@ -712,9 +794,39 @@ int foe_mixed(sxl_ctx* c, double mu, double* stats_dev) {
   return SXL_OK;
 }
 
+const MatH& final_T_mixed(const sxl_ctx* c) { return c->teff_valid ? c->hTeff : c->hT[c->nr]; }
+
+// First-order shift of the chemical potential by dmu without rerunning the
+// expansion: dD/dmu = beta D (I - D) = beta (I - T^2) / 4 exactly (the
+// perturbation commutes with H), so T_eff = T - (beta dmu / 2)(I - T^2)
+// = (beta dmu / 2) T T + T - (beta dmu / 2) I.  The neglected term is
+// (beta dmu)^2 D (I - D)(I - 2D) / 2.  The response chain keeps T_nr.
+int mu_shift_mixed(sxl_ctx* c, double dmu, double* stats_dev) {
+  const int N = c->N;
+  const MatH& T = c->hT[c->nr];
+  const float h = (float)(0.5 * c->beta * dmu);
+  SXL_TRY(gemm_tc(c, T, T, c->hTeff, h, &T, 1.f, -h, true, true));
+  c->teff_valid = true;
+  int wpb = 8, rows = 2 * N;
+  DISPATCH(c, k_rowstats_h, (rows + wpb - 1) / wpb, 32 * wpb, 0, N, rows, c->hTeff.hi,
+           c->hTeff.lo, c->diagT, c->rowsq);
+  small_kernels_density(c, c->q, stats_dev);
+  return SXL_OK;
+}
+
 int dmpt_mixed(sxl_ctx* c, const double* du) {
   const int N = c->N, nr = c->nr;
-  const bool split = true;
+  // The response products run on the hi parts alone (fp16/bf16 operands,
+  // fp32 accumulation; one product per k step): the relative error of q_v is
+  // about 7e-4 (fp16) / 5e-3 (bf16) against 2e-5 / 1e-4 in the split form,
+  // ample for the Krylov kernel, whose output only steers n.  SXL_DMPT_SPLIT=1
+  // selects the split form.
+  static int use_split = -1;
+  if (use_split < 0) {
+    const char* e = getenv("SXL_DMPT_SPLIT");
+    use_split = (e && atoi(e) == 1) ? 1 : 0;
+  }
+  const bool split = use_split == 1;
   const MatH& dS = c->hSm;
   symcombo_h(c, dS, 0.0, nullptr, 0.0, nullptr, 1.0, du, &c->hU);
   SXL_TRY(gemm_tc(c, dS, c->hS, c->hG1, 1.f, nullptr, 0.f, 0.f, false, split));
@@ -736,7 +848,7 @@ int dmpt_mixed(sxl_ctx* c, const double* du) {
 
 void dot_h0_t_mixed(sxl_ctx* c, int spin, double* out) {
   const size_t nn = (size_t)c->N * c->N;
-  const MatH& T = c->hT[c->nr];
+  const MatH& T = final_T_mixed(c);
   DISPATCH(c, k_dot_h_partial, 128, 256, 0, (long long)nn, c->H0, T.hi + spin * nn, T.lo + spin * nn,
            c->red + 2048);
   LAUNCH(k_sum_parts, 1, 256, 0, c->st, 128, c->red + 2048, out);
@@ -744,7 +856,7 @@ void dot_h0_t_mixed(sxl_ctx* c, int spin, double* out) {
 
 void density_matrix_mixed(sxl_ctx* c, double* D) {
   size_t nn = 2 * (size_t)c->N * c->N;
-  const MatH& T = c->hT[c->nr];
+  const MatH& T = final_T_mixed(c);
   DISPATCH(c, k_d_from_t_h, (unsigned)((nn + 255) / 256), 256, 0, nn, T.hi, T.lo, D, c->N);
 }
 
@@ -752,7 +864,7 @@ void density_matrix_mixed(sxl_ctx* c, double* D) {
 template <bool BF16>
 __global__ void k_split_f64(size_t n, const double* x, uint16_t* hi, uint16_t* lo) {
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i < n) st_hl<BF16>(hi, lo, i, x[i]);
+  if (i < n) st_hl<BF16>(hi, lo, i, (float)x[i]);
 }
 template <bool BF16>
 __global__ void k_join_f64(size_t n, const uint16_t* hi, const uint16_t* lo, double* x) {
@@ -798,8 +910,8 @@ static int* g_noalloc_err_ptr[NOALLOC_MAX_DEV];
 
 template <bool BF16, bool SPLIT>
 static cudaError_t noalloc_attr() {
-  return cudaFuncSetAttribute(k_tc_gemm<BF16, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)TcCfg<SPLIT>::SMEM);
+  return cudaFuncSetAttribute(k_tc_gemm<BF16, SPLIT, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)TcCfg<SPLIT, 64>::SMEM);
 }
 
 // One-time set-up per device, run with that device current: the device
@@ -879,9 +991,9 @@ static int noalloc_run(int n, uint16_t* sc, int* err, const double* A, const dou
   a.err = err;
   dim3 grid(a.ntm * a.ntn, 2);
   if (split)
-    k_tc_gemm<BF16, true><<<grid, 192, TcCfg<true>::SMEM, st>>>(maps[0], maps[1], maps[2], maps[3], a);
+    k_tc_gemm<BF16, true, 64><<<grid, 192, TcCfg<true, 64>::SMEM, st>>>(maps[0], maps[1], maps[2], maps[3], a);
   else
-    k_tc_gemm<BF16, false><<<grid, 192, TcCfg<false>::SMEM, st>>>(maps[0], maps[1], maps[2], maps[3], a);
+    k_tc_gemm<BF16, false, 64><<<grid, 192, TcCfg<false, 64>::SMEM, st>>>(maps[0], maps[1], maps[2], maps[3], a);
   k_join_f64<BF16><<<g, 256, 0, st>>>(nn, Ch, Cl, C);
   if (cudaGetLastError() != cudaSuccess) return SXL_E_CUDA;
   int flag = 0;
@@ -907,4 +1019,79 @@ extern "C" int sxl_mixed_gemm_noalloc(int n, int precision, const double* A, con
                              beta, gamma, sym, split, st);
   return noalloc_run<false>(n, g_noalloc_ptr[dev], g_noalloc_err_ptr[dev], A, B, E, C, alpha,
                             beta, gamma, sym, split, st);
+}
+
+// ---------------------------------------------------------------------------
+// entropy (see chol.cu): out[0] = sum_spins sum_a [f ln f + (1 - f) ln(1 - f)]
+// from the chain of the last expansion pass (its chemical potential; a
+// first-order shift applied afterwards is not carried into this term).
+template <bool BF16>
+__global__ void k_hl_to_f32(size_t nn, const uint16_t* hi, const uint16_t* lo, float* out,
+                            float scale) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < nn) out[i] = scale * ld_hl<BF16>(hi, lo, i);
+}
+// ld[2 (k + 1) + s] held ln det(I + T_k^2); the entropy sum wants ln det(Y_k)
+__global__ void k_negate_pairs(int nr, double* ld) {
+  int i = threadIdx.x;
+  if (i < 2 * nr) ld[2 + i] = -ld[2 + i];
+}
+template <bool BF16>
+__global__ void k_dot_hl_partial(long long len, const uint16_t* ah, const uint16_t* al,
+                                 const uint16_t* bh, const uint16_t* bl, double* part) {
+  __shared__ double sm[256];
+  double s = 0.0;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < len; i += 256LL * gridDim.x)
+    s += ld_hl_d<BF16>(ah, al, i) * ld_hl_d<BF16>(bh, bl, i);
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+__global__ void k_entropy_combine(int N, int nr, const double* ld, const double* dots, double* out) {
+  if (threadIdx.x != 0) return;
+  double tot = 0.0;
+  for (int s = 0; s < 2; ++s) {
+    double v = -N * 0.69314718055994531 + ldexp(1.0, nr - 1) * ld[s] + ldexp(1.0, nr) * dots[s];
+    for (int k = 0; k < nr; ++k) v += ldexp(1.0, nr - 1 - k) * ld[2 * (k + 1) + s];
+    tot += v;
+  }
+  out[0] = tot;
+}
+
+int entropy_mixed(sxl_ctx* c, double* out_dev) {
+  const int N = c->N, nr = c->nr;
+  const size_t nn = (size_t)N * N, nn2 = 2 * nn;
+  if (!c->fscratch) {
+    if (cudaMalloc((void**)&c->fscratch, nn2 * sizeof(float)) != cudaSuccess)
+      return sxl_fail(c, SXL_E_NOMEM, "cudaMalloc failed for the entropy scratch");
+  }
+  double* ld = c->red + 3200;   // 2 (nr + 1)
+  double* dots = c->red + 3190; // 2
+  CUDA_TRY(c, cudaMemsetAsync(ld, 0, 2 * (nr + 1) * sizeof(double), c->st));
+  const unsigned g = (unsigned)((nn2 + 255) / 256);
+  // Every factored matrix is I -/+ S_k with S_k = T_k^2 formed as a split
+  // product, so its deviation from I keeps the product's relative precision;
+  // the factorization works on that deviation (chol.cu, deviation form).
+  // ln det(I - T_0^2):  W = S_0
+  SXL_TRY(gemm_tc(c, c->hT[0], c->hT[0], c->hSm, 1.f, nullptr, 0.f, 0.f, true, true));
+  DISPATCH(c, k_hl_to_f32, g, 256, 0, nn2, c->hSm.hi, c->hSm.lo, c->fscratch, 1.f);
+  chol_logdet_dev_f32(c, N, c->fscratch, ld);
+  // ln det(Y_k) = -ln det(I + T_k^2):  W = -S_k, stored with the sign folded
+  for (int k = 0; k < nr; ++k) {
+    SXL_TRY(gemm_tc(c, c->hT[k], c->hT[k], c->hSm, 1.f, nullptr, 0.f, 0.f, true, true));
+    DISPATCH(c, k_hl_to_f32, g, 256, 0, nn2, c->hSm.hi, c->hSm.lo, c->fscratch, -1.f);
+    chol_logdet_dev_f32(c, N, c->fscratch, ld + 2 * (k + 1));
+  }
+  LAUNCH(k_negate_pairs, 1, 64, 0, c->st, nr, ld);
+  for (int s = 0; s < 2; ++s) {
+    DISPATCH(c, k_dot_hl_partial, 128, 256, 0, (long long)nn, c->hU.hi + s * nn, c->hU.lo + s * nn,
+             c->hT[nr].hi + s * nn, c->hT[nr].lo + s * nn, c->red + 2048);
+    LAUNCH(k_sum_parts, 1, 256, 0, c->st, 128, c->red + 2048, dots + s);
+  }
+  LAUNCH(k_entropy_combine, 1, 32, 0, c->st, N, nr, ld, dots, out_dev);
+  return SXL_OK;
 }

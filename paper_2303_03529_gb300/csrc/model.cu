@@ -375,10 +375,12 @@ void launch_forces(sxl_ctx* c, const double* R, const double* n, const double* q
     TsumF64 ts{c->T[c->nr], nn};
     LAUNCH(k_forces<TsumF64>, c->nat, 256, 0, c->st, c->nat, R, mc, ts, n, qspin, F, erep_atom);
   } else if (c->p.precision == SXL_MIXED_BF16) {
-    TsumH<true> ts{c->hT[c->nr].hi, c->hT[c->nr].lo, nn};
+    const MatH& T = final_T_mixed(c);
+    TsumH<true> ts{T.hi, T.lo, nn};
     LAUNCH(k_forces<TsumH<true>>, c->nat, 256, 0, c->st, c->nat, R, mc, ts, n, qspin, F, erep_atom);
   } else {
-    TsumH<false> ts{c->hT[c->nr].hi, c->hT[c->nr].lo, nn};
+    const MatH& T = final_T_mixed(c);
+    TsumH<false> ts{T.hi, T.lo, nn};
     LAUNCH(k_forces<TsumH<false>>, c->nat, 256, 0, c->st, c->nat, R, mc, ts, n, qspin, F, erep_atom);
   }
 }

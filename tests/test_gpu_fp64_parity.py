@@ -101,6 +101,9 @@ def test_forces_and_energy_terms(lib, case16):
     e_o = energy.shadow_energy(d, H0, model.repulsive_energy(w.R, w.cell, w.params))
     for k in ("band", "coul", "spin", "rep"):
         assert abs(en[k] - e_o[k]) < 1e-8, k
+    # electronic entropy through the chain log-determinants: 1e-8 eV/atom
+    assert abs(en["entropy"] - e_o["entropy"]) < 1e-8 * w.n_atoms, (en["entropy"], e_o["entropy"])
+    assert abs(en["U"] - e_o["U"]) < 1e-8 * w.n_atoms
 
 
 def test_scf_fixed_point(lib):
