@@ -255,8 +255,9 @@ static int density(sxl_ctx* c, const double* R, const double* n, double mu_guess
       return sxl_fail(c, SXL_E_NO_CONVERGENCE, "chemical potential search hit its iteration cap");
     if (err > 0) hi = mu; else lo = mu;
     // mixed forms: a small remaining shift is applied to first order (one
-    // product instead of another expansion pass)
-    if (mixed && dN > 0 && c->beta * std::fabs(err / dN) <= 3e-3) {
+    // product instead of another expansion pass); the neglected second-order
+    // term is below (beta dmu)^2 / 20 = 5e-6 per density-matrix element
+    if (mixed && dN > 0 && c->beta * std::fabs(err / dN) <= 1e-2) {
       double dmu = -err / dN;
       SXL_TRY(mu_shift_mixed(c, dmu, stats));
       SXL_TRY(sync_host(c, stats, 2));

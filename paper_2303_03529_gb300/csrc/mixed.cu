@@ -187,6 +187,7 @@ __device__ __forceinline__ void st_hl(uint16_t* hi, uint16_t* lo, size_t i, floa
 // ---------------------------------------------------------------------------
 struct TcArgs {
   int n, ntm, ntn, nk;
+  int nk_half;  // dual products: k blocks of the first pair (0 = single product)
   float alpha, beta, gamma;
   const uint16_t* Ehi;
   const uint16_t* Elo;
@@ -196,22 +197,32 @@ struct TcArgs {
   int* err;
 };
 
-template <bool SPLIT, int BK>
+// MT = 2 (plain products only): the CTA covers 256 output rows as two
+// M = 128 MMAs that share each B tile; the second accumulator takes the TMEM
+// columns the split form uses for its cross products.  Per k step the CTA
+// then loads 512 operand rows for 2 x 128 x 256 outputs instead of 384 rows
+// for 128 x 256.
+template <bool SPLIT, int BK, int MT = 1>
 struct TcCfg {
-  static constexpr uint32_t A_BYTES = TC_BM * BK * 2;
+  static_assert(!(SPLIT && MT == 2), "split products use both accumulators");
+  static constexpr uint32_t A_BYTES = TC_BM * MT * BK * 2;
+  static constexpr uint32_t A_HALF = TC_BM * BK * 2;
   static constexpr uint32_t B_BYTES = TC_BN * BK * 2;
   static constexpr uint32_t STAGE_BYTES = (A_BYTES + B_BYTES) * (SPLIT ? 2 : 1);
   static constexpr int STAGES = (int)((196608u / STAGE_BYTES) > 8 ? 8 : (196608u / STAGE_BYTES));
-  static constexpr uint32_t TMEM_COLS = SPLIT ? 512 : 256;
+  static constexpr uint32_t TMEM_COLS = (SPLIT || MT == 2) ? 512 : 256;
   static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
 };
 
-template <bool BF16, bool SPLIT, int BK = TC_BK>
+// Dual plain products (DUAL): C = A1 B1^T + A2 B2^T as one product over the
+// concatenated K dimension; the second pair comes in through the tensor maps
+// the split form uses for the lo parts.
+template <bool BF16, bool SPLIT, int BK = TC_BK, int MT = 1, bool DUAL = false>
 __global__ void __launch_bounds__(192, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
               TcArgs g) {
-  using Cfg = TcCfg<SPLIT, BK>;
+  using Cfg = TcCfg<SPLIT, BK, MT>;
   constexpr int STAGES = Cfg::STAGES;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_bar;
@@ -229,7 +240,7 @@ __global__ void __launch_bounds__(192, 1)
   const int gsz = min(g.ntm - first_m, GROUP);
   const int tm = first_m + (t % per_group) % gsz;
   const int tn = (t % per_group) / gsz;
-  const int row0 = tm * TC_BM, col0 = tn * TC_BN;
+  const int row0 = tm * TC_BM * MT, col0 = tn * TC_BN;
   if (g.sym && col0 + TC_BN - 1 < row0) return;  // owns no element with row <= col
 
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -271,6 +282,12 @@ __global__ void __launch_bounds__(192, 1)
         const uint32_t fb = smem_u32(&full_bar[s]);
         mbar_expect_tx(fb, Cfg::STAGE_BYTES);
         const uint32_t st = sbase + s * Cfg::STAGE_BYTES;
+        if (DUAL && kb >= g.nk_half) {
+          const int kx = (kb - g.nk_half) * BK;
+          tma_load_2d(st, &mAl, fb, kx, bz * g.n + row0);
+          tma_load_2d(st + Cfg::A_BYTES, &mBl, fb, kx, bz * g.n + col0);
+          continue;
+        }
         const int kx = kb * BK;
         tma_load_2d(st, &mAh, fb, kx, bz * g.n + row0);
         tma_load_2d(st + Cfg::A_BYTES, &mBh, fb, kx, bz * g.n + col0);
@@ -304,6 +321,11 @@ __global__ void __launch_bounds__(192, 1)
             umma_f16(tmem + 256, dAh + adv, dBl + adv, idesc, acc);
             umma_f16(tmem + 256, dAl + adv, dBh + adv, idesc, 1u);
           }
+          if (MT == 2) {
+            // rows 128..255 of the A tile start 128 rows (A_HALF bytes) later
+            const uint64_t dA2 = dAh + (uint64_t)(Cfg::A_HALF >> 4);
+            umma_f16(tmem + 256, dA2 + adv, dBh + adv, idesc, acc);
+          }
         }
         umma_commit(smem_u32(&empty_bar[s]));
       }
@@ -314,15 +336,18 @@ __global__ void __launch_bounds__(192, 1)
     // Epilogue in fp32: acc0 + acc1 2^-12 keeps 24 bits, and w - rn(w) of the
     // hi/lo split is exact in fp32, so no fp64 arithmetic is needed here.
     const int q = warp & 3;  // TMEM lane quarter this warp may access
-    const int row = row0 + q * 32 + lane;
     bool ok = mbar_wait(smem_u32(&acc_bar), 0, &s_abort, true);
     ok = __all_sync(0xffffffffu, ok);
     tc_fence_after();
     if (ok) {
       const size_t mat = (size_t)bz * g.n * g.n;
-      for (int cc = 0; cc < TC_BN; cc += 32) {
+      for (int it = 0; it < MT * (TC_BN / 32); ++it) {
+      const int mt = it / (TC_BN / 32);
+      const int cc = (it % (TC_BN / 32)) * 32;
+      const int row = row0 + mt * TC_BM + q * 32 + lane;
+      {
         uint32_t a0[32], a1[32];
-        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)cc;
+        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cc + 256 * mt);
         tmem_ld32(ta, a0);
         if (SPLIT) tmem_ld32(ta + 256, a1);
         tmem_wait_ld();
@@ -389,6 +414,7 @@ __global__ void __launch_bounds__(192, 1)
           }
         }
       }
+      }
     }
   }
 
@@ -443,12 +469,12 @@ static int make_map(sxl_ctx* c, CUtensorMap* m, const uint16_t* base, int n, int
   return SXL_OK;
 }
 
-template <bool BF16, bool SPLIT, int BK>
+template <bool BF16, bool SPLIT, int BK, int MT = 1, bool DUAL = false>
 static int launch_tc(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a) {
-  using Cfg = TcCfg<SPLIT, BK>;
+  using Cfg = TcCfg<SPLIT, BK, MT>;
   static bool attr = false;
   if (!attr) {
-    CUDA_TRY(c, cudaFuncSetAttribute(k_tc_gemm<BF16, SPLIT, BK>,
+    CUDA_TRY(c, cudaFuncSetAttribute(k_tc_gemm<BF16, SPLIT, BK, MT, DUAL>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
     attr = true;
   }
@@ -459,7 +485,8 @@ static int launch_tc(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a) {
     e1 = ev_get(c);
     CUDA_TRY(c, cudaEventRecord(e0, c->st));
   }
-  k_tc_gemm<BF16, SPLIT, BK><<<grid, 192, Cfg::SMEM, c->st>>>(maps[0], maps[1], maps[2], maps[3], a);
+  k_tc_gemm<BF16, SPLIT, BK, MT, DUAL><<<grid, 192, Cfg::SMEM, c->st>>>(maps[0], maps[1], maps[2],
+                                                                      maps[3], a);
   ++g_sxl_launches;
   if (c->time_tc) {
     CUDA_TRY(c, cudaEventRecord(e1, c->st));
@@ -467,11 +494,13 @@ static int launch_tc(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a) {
     double tiles = 0;
     for (int tm = 0; tm < a.ntm; ++tm)
       for (int tn = 0; tn < a.ntn; ++tn)
-        if (!a.sym || tn * TC_BN + TC_BN - 1 >= tm * TC_BM) tiles += 1;
+        if (!a.sym || tn * TC_BN + TC_BN - 1 >= tm * TC_BM * MT) tiles += 1;
     double n = a.n;
-    double mma = 2.0 * tiles * 2.0 * TC_BM * TC_BN * n * (SPLIT ? 3.0 : 1.0);
+    double mma = 2.0 * tiles * 2.0 * TC_BM * MT * TC_BN * n * (SPLIT ? 3.0 : 1.0);
+    const double kfac = DUAL ? 2.0 : 1.0;  // dual products run over 2n
+    mma *= kfac;
     double owned = a.sym ? n * (n + 1) / 2 : n * n;
-    double f32 = 2.0 * 2.0 * owned * n;  // both spins, 2 n flops per owned element
+    double f32 = 2.0 * 2.0 * owned * n * kfac;  // both spins, 2 n (4 n dual) per owned element
     c->ev_pending.push_back({e0, e1, mma, f32 * (SPLIT ? 3.0 : 1.0), f32});
   }
   return SXL_OK;
@@ -492,16 +521,25 @@ int gemm_tc(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C, float alpha
     bk_env = e ? atoi(e) : 0;
   }
   const int bk = (bk_env == 32 || bk_env == 64) ? bk_env : (split ? 32 : 64);
+  // plain products cover 256 rows per CTA (two M = 128 MMAs per B tile);
+  // SXL_TC_MT=1 restores 128-row tiles
+  static int mt_env = -1;
+  if (mt_env < 0) {
+    const char* e = getenv("SXL_TC_MT");
+    mt_env = e ? atoi(e) : 0;
+  }
+  const int mt = split ? 1 : (mt_env == 1 ? 1 : 2);
   CUtensorMap maps[4];
-  SXL_TRY(make_map(c, &maps[0], A.hi, n, TC_BM, bf16, bk));
-  SXL_TRY(make_map(c, &maps[1], A.lo, n, TC_BM, bf16, bk));
+  SXL_TRY(make_map(c, &maps[0], A.hi, n, TC_BM * mt, bf16, bk));
+  SXL_TRY(make_map(c, &maps[1], A.lo, n, TC_BM * mt, bf16, bk));
   SXL_TRY(make_map(c, &maps[2], B.hi, n, TC_BN, bf16, bk));
   SXL_TRY(make_map(c, &maps[3], B.lo, n, TC_BN, bf16, bk));
   TcArgs a;
   a.n = n;
-  a.ntm = (n + TC_BM - 1) / TC_BM;
+  a.ntm = (n + TC_BM * mt - 1) / (TC_BM * mt);
   a.ntn = (n + TC_BN - 1) / TC_BN;
   a.nk = n / bk;
+  a.nk_half = 0;
   a.alpha = alpha;
   a.beta = beta;
   a.gamma = gamma;
@@ -512,12 +550,47 @@ int gemm_tc(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C, float alpha
   a.sym = sym ? 1 : 0;
   a.err = g_tc_err;
   c->n_gemm++;
-  if (bk == 64) {
-    if (bf16) return split ? launch_tc<true, true, 64>(c, maps, a) : launch_tc<true, false, 64>(c, maps, a);
-    return split ? launch_tc<false, true, 64>(c, maps, a) : launch_tc<false, false, 64>(c, maps, a);
+  if (split) {
+    if (bk == 64) return bf16 ? launch_tc<true, true, 64>(c, maps, a) : launch_tc<false, true, 64>(c, maps, a);
+    return bf16 ? launch_tc<true, true, 32>(c, maps, a) : launch_tc<false, true, 32>(c, maps, a);
   }
-  if (bf16) return split ? launch_tc<true, true, 32>(c, maps, a) : launch_tc<true, false, 32>(c, maps, a);
-  return split ? launch_tc<false, true, 32>(c, maps, a) : launch_tc<false, false, 32>(c, maps, a);
+  if (mt == 2) {
+    if (bk == 64) return bf16 ? launch_tc<true, false, 64, 2>(c, maps, a) : launch_tc<false, false, 64, 2>(c, maps, a);
+    return bf16 ? launch_tc<true, false, 32, 2>(c, maps, a) : launch_tc<false, false, 32, 2>(c, maps, a);
+  }
+  if (bk == 64) return bf16 ? launch_tc<true, false, 64>(c, maps, a) : launch_tc<false, false, 64>(c, maps, a);
+  return bf16 ? launch_tc<true, false, 32>(c, maps, a) : launch_tc<false, false, 32>(c, maps, a);
+}
+
+// C = alpha (A1 B1^T + A2 B2^T) + beta E + gamma I (plain products on the hi
+// parts), one pass over the concatenated K dimension.
+int gemm_tc_dual(sxl_ctx* c, const MatH& A1, const MatH& B1, const MatH& A2, const MatH& B2,
+                 const MatH& C, float alpha, const MatH* E, float beta, float gamma, bool sym) {
+  const bool bf16 = c->p.precision == SXL_MIXED_BF16;
+  const int n = c->N, bk = 64, mt = 2;
+  CUtensorMap maps[4];
+  SXL_TRY(make_map(c, &maps[0], A1.hi, n, TC_BM * mt, bf16, bk));
+  SXL_TRY(make_map(c, &maps[1], A2.hi, n, TC_BM * mt, bf16, bk));
+  SXL_TRY(make_map(c, &maps[2], B1.hi, n, TC_BN, bf16, bk));
+  SXL_TRY(make_map(c, &maps[3], B2.hi, n, TC_BN, bf16, bk));
+  TcArgs a;
+  a.n = n;
+  a.ntm = (n + TC_BM * mt - 1) / (TC_BM * mt);
+  a.ntn = (n + TC_BN - 1) / TC_BN;
+  a.nk_half = n / bk;
+  a.nk = 2 * a.nk_half;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.gamma = gamma;
+  a.Ehi = E ? E->hi : nullptr;
+  a.Elo = E ? E->lo : nullptr;
+  a.Chi = C.hi;
+  a.Clo = C.lo;
+  a.sym = sym ? 1 : 0;
+  a.err = g_tc_err;
+  c->n_gemm++;
+  return bf16 ? launch_tc<true, false, 64, 2, true>(c, maps, a)
+              : launch_tc<false, false, 64, 2, true>(c, maps, a);
 }
 
 // ---------------------------------------------------------------------------
@@ -836,8 +909,13 @@ int dmpt_mixed(sxl_ctx* c, const double* du) {
   const MatH* dB = &c->hdTb;
   symcombo_h(c, *dA, 0.0, nullptr, 0.5, &c->hG1, 0.5, du, &c->hQ);
   for (int k = 0; k < nr; ++k) {
-    SXL_TRY(gemm_tc(c, c->hT[k], *dA, c->hP, 1.f, nullptr, 0.f, 0.f, false, split));
-    symcombo_h(c, c->hSm, 0.0, nullptr, 1.0, &c->hP, 0.0, nullptr, nullptr);
+    if (split) {
+      SXL_TRY(gemm_tc(c, c->hT[k], *dA, c->hP, 1.f, nullptr, 0.f, 0.f, false, split));
+      symcombo_h(c, c->hSm, 0.0, nullptr, 1.0, &c->hP, 0.0, nullptr, nullptr);
+    } else {
+      // S = T dT + dT T in one symmetric product over [T | dT] [dT | T]^T
+      SXL_TRY(gemm_tc_dual(c, c->hT[k], *dA, *dA, c->hT[k], c->hSm, 1.f, nullptr, 0.f, 0.f, true));
+    }
     SXL_TRY(gemm_tc(c, c->hT[k + 1], c->hSm, c->hG1, -0.5f, dA, 1.f, 0.f, false, split));
     SXL_TRY(gemm_tc(c, c->hG1, c->hY[k], *dB, 2.f, nullptr, 0.f, 0.f, true, split));
     std::swap(dA, dB);
