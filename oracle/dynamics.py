@@ -19,6 +19,13 @@ mixing (coefficient 0.06) until the residual RMS drops below 0.05, then the
 exact kernel J^{-1} at that point is taken as K0 and kept (Sec. III.C,
 Fig. SCF caption).  Ranks are adaptive (stop once the relative least-squares
 residual is below 0.1, at most `rank`).
+
+The comparison mixers of Fig. SCF: plain linear mixing (0.06) throughout,
+and Pulay's DIIS switched on at the same 0.05 threshold.  DIIS keeps the last
+`diis_hist` pairs (n_i, f_i), takes the coefficients c minimizing
+|sum c_i f_i| subject to sum c_i = 1 (Lagrange system with B_ij = f_i . f_j)
+and sets n_new = sum c_i (n_i + diis_mix f_i); the paper gives neither the
+history length nor the mixing, so 8 and 0.1 are parameters.
 """
 from __future__ import annotations
 
@@ -43,9 +50,26 @@ def rms(x):
     return float(np.sqrt(np.mean(np.asarray(x) ** 2)))
 
 
+def diis_update(ns, fs, mix):
+    """Pulay step from the histories ns, fs (lists of vectors)."""
+    m = len(fs)
+    B = np.empty((m + 1, m + 1))
+    for i in range(m):
+        for j in range(m):
+            B[i, j] = fs[i] @ fs[j]
+    B[m, :m] = B[:m, m] = 1.0
+    B[m, m] = 0.0
+    rhs = np.zeros(m + 1)
+    rhs[m] = 1.0
+    c = np.linalg.solve(B, rhs)[:m]
+    return sum(ci * (ni + mix * fi) for ci, ni, fi in zip(c, ns, fs))
+
+
 def scf(R, cell, n0, p, tol=1e-8, max_iter=200, rank=None, lin_mix=0.06,
-        kernel_on=0.05, rel_tol=0.1, return_history=False):
-    """SCF with linear mixing, then the Krylov quasi-Newton kernel mixer."""
+        kernel_on=0.05, rel_tol=0.1, return_history=False, mixer="kernel",
+        diis_hist=8, diis_mix=0.1):
+    """SCF with linear mixing, then the Krylov quasi-Newton kernel mixer
+    (mixer="kernel"), Pulay DIIS ("diis") or linear mixing only ("linear")."""
     rank = p.krylov_rank if rank is None else rank
     H0 = model.build_h0(R, cell, p)
     G = model.gamma_matrix(R, cell, p)
@@ -53,6 +77,8 @@ def scf(R, cell, n0, p, tol=1e-8, max_iter=200, rank=None, lin_mix=0.06,
     K0 = None
     mu = None
     hist = []
+    dn, df = [], []
+    diis_on = False
     for it in range(max_iter):
         dens = electronic.Density(H0, G, n, p, mu_guess=mu)
         mu = dens.mu
@@ -64,8 +90,16 @@ def scf(R, cell, n0, p, tol=1e-8, max_iter=200, rank=None, lin_mix=0.06,
             if return_history:
                 out["history"] = hist
             return out
-        if K0 is None and r >= kernel_on:
+        if mixer == "linear" or (mixer == "diis" and not diis_on and r >= kernel_on) or \
+                (mixer == "kernel" and K0 is None and r >= kernel_on):
             n = n + lin_mix * f
+            continue
+        if mixer == "diis":
+            diis_on = True
+            dn.append(n.copy())
+            df.append(f.copy())
+            dn, df = dn[-diis_hist:], df[-diis_hist:]
+            n = diis_update(dn, df, diis_mix)
             continue
         if K0 is None:
             K0 = kernel.exact_kernel(dens)

@@ -254,11 +254,22 @@ static int density(sxl_ctx* c, const double* R, const double* n, double mu_guess
     if (it + 1 >= maxit)
       return sxl_fail(c, SXL_E_NO_CONVERGENCE, "chemical potential search hit its iteration cap");
     if (err > 0) hi = mu; else lo = mu;
-    // mixed forms: a small remaining shift is applied to first order (one
-    // product instead of another expansion pass); the neglected second-order
-    // term is below (beta dmu)^2 / 20 = 5e-6 per density-matrix element
-    if (mixed && dN > 0 && c->beta * std::fabs(err / dN) <= 1e-2) {
+    // mixed forms: the remaining shift of mu is applied to the final T by
+    // the tanh addition theorem (one well-conditioned inverse instead of
+    // another expansion pass); a leftover of beta |dmu| <= 1e-2 is then
+    // applied to first order (neglected term <= (beta dmu)^2 / 20).
+    if (mixed && dN > 0 && c->beta * std::fabs(err / dN) <= 1.0) {
       double dmu = -err / dN;
+      if (c->beta * std::fabs(dmu) > 1e-2) {
+        SXL_TRY(mu_shift_exact_mixed(c, dmu, stats));
+        SXL_TRY(sync_host(c, stats, 2));
+        mu += dmu;
+        if (dbg)
+          fprintf(stderr, "[sxl] mu exact shift %.3e -> N %.10f\n", dmu, c->hred[0]);
+        double err2 = c->hred[0] - Ne;
+        dmu = (c->hred[1] > 0) ? -err2 / c->hred[1] : 0.0;
+        if (std::fabs(err2) < tol) { c->last_N = c->hred[0]; break; }
+      }
       SXL_TRY(mu_shift_mixed(c, dmu, stats));
       SXL_TRY(sync_host(c, stats, 2));
       mu += dmu;
@@ -448,6 +459,7 @@ int sxl_create(const sxl_params* prm, void* stream, sxl_ctx** out) {
   c->mu = NAN;
   c->mu_prev = NAN;
   c->teff_valid = false;
+  c->shift_tau = 0.0;
   c->fscratch = nullptr;
   c->state_ready = c->evaluated = c->have_density = c->h0_valid = false;
   c->nr = 0; c->nr_cap = 0;

@@ -66,8 +66,10 @@ struct sxl_ctx {
   MatH hU, hS, hQ, hX0, hX1, hP, hSm, hdTa, hdTb, hG1;
   std::vector<MatH> hT, hY;
   MatH hTeff;             // T_nr after a first-order chemical-potential shift
+  MatH hXs;               // (I - tau T_nr)^{-1} of the last exact shift
   float* fscratch;        // 2 N^2 fp32 (entropy factorizations, mixed forms)
   bool teff_valid;        // hTeff (not hT[nr]) holds the final density
+  double shift_tau;       // tanh(beta dmu / 2) of the exact shift in hTeff (0: none)
   double mu_prev;         // chemical potential of the previous MD step (NaN: none)
 
   double *diagT, *rowsq, *chi;  // 2N each
@@ -181,6 +183,7 @@ int sxl_mixed_supported(sxl_ctx* c);
 void sxl_mixed_free(sxl_ctx* c);
 int foe_mixed(sxl_ctx* c, double mu, double* stats_dev);
 int mu_shift_mixed(sxl_ctx* c, double dmu, double* stats_dev);
+int mu_shift_exact_mixed(sxl_ctx* c, double dmu, double* stats_dev);
 const MatH& final_T_mixed(const sxl_ctx* c);
 int dmpt_mixed(sxl_ctx* c, const double* du);
 void dot_h0_t_mixed(sxl_ctx* c, int spin, double* out);

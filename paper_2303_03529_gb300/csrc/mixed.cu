@@ -614,48 +614,6 @@ __global__ void k_build_u_h(int nat, const double* __restrict__ H0, const double
 }
 
 template <bool BF16>
-__global__ void k_axpy_diag_h(size_t total, int n, uint16_t* ohi, uint16_t* olo, double a,
-                              const uint16_t* xhi, const uint16_t* xlo, double g) {
-  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i >= total) return;
-  size_t e = i % ((size_t)n * n);
-  float v = (float)a * ld_hl<BF16>(xhi, xlo, i);
-  if (e / n == e % n) v += (float)g;
-  st_hl<BF16>(ohi, olo, i, v);
-}
-
-// out = a X + b (Y + Y^T) + cc (w_i + w_j) Z
-template <bool BF16>
-__global__ void k_symcombo_h(int n, uint16_t* ohi, uint16_t* olo, double a, const uint16_t* xhi,
-                             const uint16_t* xlo, double b, const uint16_t* yhi,
-                             const uint16_t* ylo, double cc, const double* w, const uint16_t* zhi,
-                             const uint16_t* zlo) {
-  const size_t bs = (size_t)n * n * blockIdx.z;
-  __shared__ float tile[32][33];
-  int bx = blockIdx.x * 32, by = blockIdx.y * 32;
-  int tx = threadIdx.x, ty = threadIdx.y;
-  if (yhi) {
-    for (int k = ty; k < 32; k += 8) {
-      int r = bx + k, col = by + tx;
-      tile[k][tx] = (r < n && col < n) ? ld_hl<BF16>(yhi, ylo, bs + (size_t)r * n + col) : 0.f;
-    }
-  }
-  __syncthreads();
-  const double* wv = w ? w + (size_t)n * blockIdx.z : nullptr;
-  const float fa = (float)a, fb = (float)b, fc = (float)cc;
-  for (int k = ty; k < 32; k += 8) {
-    int r = by + k, col = bx + tx;
-    if (r >= n || col >= n) continue;
-    size_t idx = bs + (size_t)r * n + col;
-    float v = 0.f;
-    if (xhi) v += fa * ld_hl<BF16>(xhi, xlo, idx);
-    if (yhi) v += fb * (ld_hl<BF16>(yhi, ylo, idx) + tile[tx][k]);
-    if (zhi) v += fc * (float)(wv[r] + wv[col]) * ld_hl<BF16>(zhi, zlo, idx);
-    st_hl<BF16>(ohi, olo, idx, v);
-  }
-}
-
-template <bool BF16>
 __global__ void k_rowstats_h(int n, int rows, const uint16_t* hi, const uint16_t* lo, double* diag,
                              double* rowsq) {
   int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
@@ -729,19 +687,100 @@ __global__ void k_d_from_t_h(size_t nn, const uint16_t* hi, const uint16_t* lo, 
       LAUNCH(KERN<false>, grid, block, smem, (c)->st, __VA_ARGS__);                 \
   } while (0)
 
+// out = a X + b (Y + Y^T) + cc (w_i + w_j) Z on both spin blocks, for
+// n % 64 == 0 with element pairs: 4-byte loads and stores of two 16-bit
+// values, 32 x 64 output tiles, Y^T through a shared-memory transpose.
+template <bool BF16>
+__device__ __forceinline__ void ld_pair(const uint16_t* hi, const uint16_t* lo, size_t i,
+                                        float& a, float& b) {
+  uint32_t h = *reinterpret_cast<const uint32_t*>(hi + i);
+  uint32_t l = *reinterpret_cast<const uint32_t*>(lo + i);
+  a = HL<BF16>::f((uint16_t)(h & 0xffffu)) + HL<BF16>::f((uint16_t)(l & 0xffffu)) * LO_INV;
+  b = HL<BF16>::f((uint16_t)(h >> 16)) + HL<BF16>::f((uint16_t)(l >> 16)) * LO_INV;
+}
+template <bool BF16>
+__device__ __forceinline__ void st_pair(uint16_t* hi, uint16_t* lo, size_t i, float a, float b) {
+  uint16_t ha = HL<BF16>::b(a), hb = HL<BF16>::b(b);
+  uint16_t la = HL<BF16>::b((a - HL<BF16>::f(ha)) * LO_SCALE);
+  uint16_t lb = HL<BF16>::b((b - HL<BF16>::f(hb)) * LO_SCALE);
+  *reinterpret_cast<uint32_t*>(hi + i) = (uint32_t)ha | ((uint32_t)hb << 16);
+  *reinterpret_cast<uint32_t*>(lo + i) = (uint32_t)la | ((uint32_t)lb << 16);
+}
+
+template <bool BF16>
+__global__ void k_symcombo2_h(int n, uint16_t* ohi, uint16_t* olo, float a, const uint16_t* xhi,
+                              const uint16_t* xlo, float b, const uint16_t* yhi,
+                              const uint16_t* ylo, float cc, const double* w,
+                              const uint16_t* zhi, const uint16_t* zlo) {
+  const size_t bs = (size_t)n * n * blockIdx.z;
+  __shared__ float tile[64][33];
+  const int bx = blockIdx.x * 64, by = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  if (yhi) {
+    // rows bx..bx+63, columns by..by+31 of Y: the transpose of the output tile
+    for (int e = ty * 32 + tx; e < 64 * 16; e += 256) {
+      int rr = e / 16, cp = e % 16;
+      float v0, v1;
+      ld_pair<BF16>(yhi, ylo, bs + (size_t)(bx + rr) * n + by + 2 * cp, v0, v1);
+      tile[rr][2 * cp] = v0;
+      tile[rr][2 * cp + 1] = v1;
+    }
+  }
+  __syncthreads();
+  const double* wv = w ? w + (size_t)n * blockIdx.z : nullptr;
+  const int c0 = bx + 2 * tx;
+  for (int k = ty; k < 32; k += 8) {
+    const int r = by + k;
+    const size_t idx = bs + (size_t)r * n + c0;
+    float v0 = 0.f, v1 = 0.f, t0, t1;
+    if (xhi) {
+      ld_pair<BF16>(xhi, xlo, idx, t0, t1);
+      v0 += a * t0;
+      v1 += a * t1;
+    }
+    if (yhi) {
+      ld_pair<BF16>(yhi, ylo, idx, t0, t1);
+      v0 += b * (t0 + tile[2 * tx][k]);
+      v1 += b * (t1 + tile[2 * tx + 1][k]);
+    }
+    if (zhi) {
+      ld_pair<BF16>(zhi, zlo, idx, t0, t1);
+      v0 += cc * (float)(wv[r] + wv[c0]) * t0;
+      v1 += cc * (float)(wv[r] + wv[c0 + 1]) * t1;
+    }
+    st_pair<BF16>(ohi, olo, idx, v0, v1);
+  }
+}
+
 static void symcombo_h(sxl_ctx* c, const MatH& out, double a, const MatH* X, double b,
                        const MatH* Y, double cc, const double* w, const MatH* Z) {
-  int n = c->N;
-  dim3 grid((n + 31) / 32, (n + 31) / 32, 2), block(32, 8);
-  DISPATCH(c, k_symcombo_h, grid, block, 0, n, out.hi, out.lo, a, X ? X->hi : nullptr,
-           X ? X->lo : nullptr, b, Y ? Y->hi : nullptr, Y ? Y->lo : nullptr, cc, w,
+  int n = c->N;  // the mixed forms require n % 64 == 0
+  dim3 grid(n / 64, n / 32, 2), block(32, 8);
+  DISPATCH(c, k_symcombo2_h, grid, block, 0, n, out.hi, out.lo, (float)a, X ? X->hi : nullptr,
+           X ? X->lo : nullptr, (float)b, Y ? Y->hi : nullptr, Y ? Y->lo : nullptr, (float)cc, w,
            Z ? Z->hi : nullptr, Z ? Z->lo : nullptr);
 }
 
+template <bool BF16>
+__global__ void k_axpy_diag2_h(size_t pairs, int n, uint16_t* ohi, uint16_t* olo, float a,
+                               const uint16_t* xhi, const uint16_t* xlo, float g) {
+  size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (p >= pairs) return;
+  size_t i = 2 * p;
+  size_t e = i % ((size_t)n * n);
+  float v0, v1;
+  ld_pair<BF16>(xhi, xlo, i, v0, v1);
+  v0 *= a;
+  v1 *= a;
+  if (e / n == e % n) v0 += g;            // n even: the diagonal element is
+  if ((e + 1) / n == (e + 1) % n) v1 += g;  // either of the pair
+  st_pair<BF16>(ohi, olo, i, v0, v1);
+}
+
 static void axpy_diag_h(sxl_ctx* c, const MatH& out, double a, const MatH& X, double g) {
-  size_t total = 2 * (size_t)c->N * c->N;
-  DISPATCH(c, k_axpy_diag_h, (unsigned)((total + 255) / 256), 256, 0, total, c->N, out.hi, out.lo,
-           a, X.hi, X.lo, g);
+  size_t pairs = (size_t)c->N * c->N;  // 2 spins x N^2 / 2
+  DISPATCH(c, k_axpy_diag2_h, (unsigned)((pairs + 255) / 256), 256, 0, pairs, c->N, out.hi,
+           out.lo, (float)a, X.hi, X.lo, (float)g);
 }
 
 static int halloc(sxl_ctx* c, MatH* m) {
@@ -774,7 +813,7 @@ int sxl_mixed_supported(sxl_ctx* c) {
     CUDA_TRY(c, cudaMemset(g_tc_err, 0, sizeof(int)));
   }
   MatH* ms[] = {&c->hU, &c->hS, &c->hQ, &c->hX0, &c->hX1, &c->hP, &c->hSm, &c->hdTa, &c->hdTb, &c->hG1,
-                &c->hTeff};
+                &c->hTeff, &c->hXs};
   for (MatH* m : ms) SXL_TRY(halloc(c, m));
   c->teff_valid = false;
   return SXL_OK;
@@ -782,7 +821,7 @@ int sxl_mixed_supported(sxl_ctx* c) {
 
 void sxl_mixed_free(sxl_ctx* c) {
   MatH* ms[] = {&c->hU, &c->hS, &c->hQ, &c->hX0, &c->hX1, &c->hP, &c->hSm, &c->hdTa, &c->hdTb, &c->hG1,
-                &c->hTeff};
+                &c->hTeff, &c->hXs};
   for (MatH* m : ms) hfree(*m);
   if (c->fscratch) cudaFree(c->fscratch);
   c->fscratch = nullptr;
@@ -834,6 +873,7 @@ int foe_mixed(sxl_ctx* c, double mu, double* stats_dev) {
   // Newton-Schulz error bound of 1e-7 is at that floor
   const double tol = 1e-7;
   c->teff_valid = false;
+  c->shift_tau = 0.0;
   c->ns_iters.assign(nr, 0);
   for (int k = 0; k < nr; ++k) {
     const MatH& Sq = c->hSm;
@@ -849,12 +889,18 @@ int foe_mixed(sxl_ctx* c, double mu, double* stats_dev) {
     axpy_diag_h(c, *cur, -ci * ci, Sq, 2.0 * ci - ci * ci);
     for (int it = 0; it < j; ++it) {
       const MatH* nxt = (it == j - 1) ? &c->hY[k] : (cur == &c->hX0 ? &c->hX1 : &c->hX0);
-      // Newton-Schulz corrects its own rounding: every iteration but the last
-      // runs on the hi parts alone (one product per k step); the last one, in
-      // split form, squares the remaining error down to the split floor
-      const bool sp = split && (it == j - 1);
-      SXL_TRY(gemm_tc(c, *cur, Sq, c->hP, 1.f, cur, 1.f, 0.f, false, sp));
-      SXL_TRY(gemm_tc(c, c->hP, *cur, *nxt, -1.f, cur, 2.f, 0.f, true, sp));
+      if (it < j - 1 || !split) {
+        // Newton-Schulz corrects its own rounding: every iteration but the
+        // last runs on the hi parts alone (one product per k step)
+        SXL_TRY(gemm_tc(c, *cur, Sq, c->hP, 1.f, cur, 1.f, 0.f, false, false));
+        SXL_TRY(gemm_tc(c, c->hP, *cur, *nxt, -1.f, cur, 2.f, 0.f, true, false));
+      } else {
+        // last iteration as a refinement X' = X + R X: the residual
+        // R = I - X (I + T^2) needs the split products; R is small, so R X
+        // runs on the hi parts (its error is 2^-11 |R|)
+        SXL_TRY(gemm_tc(c, *cur, Sq, c->hP, -1.f, cur, -1.f, 1.f, false, true));
+        SXL_TRY(gemm_tc(c, c->hP, *cur, *nxt, 1.f, cur, 1.f, 0.f, true, false));
+      }
       cur = nxt;
     }
     SXL_TRY(gemm_tc(c, c->hT[k], c->hY[k], c->hT[k + 1], 2.f, nullptr, 0.f, 0.f, true, split));
@@ -869,6 +915,48 @@ int foe_mixed(sxl_ctx* c, double mu, double* stats_dev) {
 
 const MatH& final_T_mixed(const sxl_ctx* c) { return c->teff_valid ? c->hTeff : c->hT[c->nr]; }
 
+// Exact shift of the chemical potential by dmu: with y = beta (eps - mu)/2
+// and s = beta dmu / 2, tanh(y - s) = (t - tau) / (1 - t tau), tau = tanh(s),
+// so T' = (T - tau I)(I - tau T)^{-1}.  The inverse comes from Newton-Schulz
+// started at I + tau T (error tau^2 T^2); tau is small in MD, so two or three
+// iterations suffice.  The result replaces the final T (hTeff); the response
+// chain keeps T_nr.  c->shift_tau records tau for the entropy.
+int mu_shift_exact_mixed(sxl_ctx* c, double dmu, double* stats_dev) {
+  const int N = c->N;
+  const MatH& T = c->hT[c->nr];
+  const double tau = std::tanh(0.5 * c->beta * dmu);
+  // M = I - tau T (in hSm), X = I + tau T
+  axpy_diag_h(c, c->hSm, -tau, T, 1.0);
+  axpy_diag_h(c, c->hX0, tau, T, 1.0);
+  const MatH* cur = &c->hX0;
+  double e = tau * tau;
+  int it = 0;
+  while (e > 1e-7 && it < 6) {
+    const MatH* nxt = (cur == &c->hX0) ? &c->hX1 : &c->hX0;
+    if (e > 1e-3) {
+      SXL_TRY(gemm_tc(c, *cur, c->hSm, c->hP, 1.f, nullptr, 0.f, 0.f, false, false));
+      SXL_TRY(gemm_tc(c, c->hP, *cur, *nxt, -1.f, cur, 2.f, 0.f, true, false));
+    } else {
+      SXL_TRY(gemm_tc(c, *cur, c->hSm, c->hP, -1.f, nullptr, 0.f, 1.f, false, true));
+      SXL_TRY(gemm_tc(c, c->hP, *cur, *nxt, 1.f, cur, 1.f, 0.f, true, false));
+    }
+    cur = nxt;
+    e = std::max(e * e, 1e-14);
+    ++it;
+  }
+  // T' = T X - tau X (T and X commute: a symmetric product)
+  SXL_TRY(gemm_tc(c, T, *cur, c->hTeff, 1.f, cur, (float)(-tau), 0.f, true, true));
+  // keep X = (I - tau T)^{-1}: the response maps dT to dT' = (1 - tau^2) X dT X
+  std::swap(c->hXs, cur == &c->hX0 ? c->hX0 : c->hX1);
+  c->teff_valid = true;
+  c->shift_tau = tau;
+  int wpb = 8, rows = 2 * N;
+  DISPATCH(c, k_rowstats_h, (rows + wpb - 1) / wpb, 32 * wpb, 0, N, rows, c->hTeff.hi,
+           c->hTeff.lo, c->diagT, c->rowsq);
+  small_kernels_density(c, c->q, stats_dev);
+  return SXL_OK;
+}
+
 // First-order shift of the chemical potential by dmu without rerunning the
 // expansion: dD/dmu = beta D (I - D) = beta (I - T^2) / 4 exactly (the
 // perturbation commutes with H), so T_eff = T - (beta dmu / 2)(I - T^2)
@@ -876,9 +964,15 @@ const MatH& final_T_mixed(const sxl_ctx* c) { return c->teff_valid ? c->hTeff : 
 // (beta dmu)^2 D (I - D)(I - 2D) / 2.  The response chain keeps T_nr.
 int mu_shift_mixed(sxl_ctx* c, double dmu, double* stats_dev) {
   const int N = c->N;
-  const MatH& T = c->hT[c->nr];
   const float h = (float)(0.5 * c->beta * dmu);
-  SXL_TRY(gemm_tc(c, T, T, c->hTeff, h, &T, 1.f, -h, true, true));
+  if (c->teff_valid) {
+    // on top of an exact shift: T_eff2 from T_eff, via hSm, then swap
+    SXL_TRY(gemm_tc(c, c->hTeff, c->hTeff, c->hSm, h, &c->hTeff, 1.f, -h, true, true));
+    std::swap(c->hSm, c->hTeff);
+  } else {
+    const MatH& T = c->hT[c->nr];
+    SXL_TRY(gemm_tc(c, T, T, c->hTeff, h, &T, 1.f, -h, true, true));
+  }
   c->teff_valid = true;
   int wpb = 8, rows = 2 * N;
   DISPATCH(c, k_rowstats_h, (rows + wpb - 1) / wpb, 32 * wpb, 0, N, rows, c->hTeff.hi,
@@ -918,6 +1012,14 @@ int dmpt_mixed(sxl_ctx* c, const double* du) {
     }
     SXL_TRY(gemm_tc(c, c->hT[k + 1], c->hSm, c->hG1, -0.5f, dA, 1.f, 0.f, false, split));
     SXL_TRY(gemm_tc(c, c->hG1, c->hY[k], *dB, 2.f, nullptr, 0.f, 0.f, true, split));
+    std::swap(dA, dB);
+  }
+  if (c->teff_valid && c->shift_tau != 0.0) {
+    // the final T was shifted exactly (tanh addition): the same map carries
+    // the response, dT' = (1 - tau^2) X dT X with X = (I - tau T)^{-1}
+    const float f = (float)(1.0 - c->shift_tau * c->shift_tau);
+    SXL_TRY(gemm_tc(c, c->hXs, *dA, c->hG1, 1.f, nullptr, 0.f, 0.f, false, split));
+    SXL_TRY(gemm_tc(c, c->hG1, c->hXs, *dB, f, nullptr, 0.f, 0.f, true, split));
     std::swap(dA, dB);
   }
   DISPATCH(c, k_diag2_h, (2 * N + 255) / 256, 256, 0, N, dA->hi, dA->lo, c->diagT + 2 * N);
@@ -1129,15 +1231,42 @@ __global__ void k_dot_hl_partial(long long len, const uint16_t* ah, const uint16
   }
   if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
 }
-__global__ void k_entropy_combine(int N, int nr, const double* ld, const double* dots, double* out) {
+// sum_a s(f_a) = -N ln 2 - Tr ln cosh(Y') + Tr(Y' T') per spin, with
+// Y' = Y - sh I after an exact shift (sh = beta dmu / 2, 0 without one):
+// Tr ln cosh(Y') = Tr ln cosh(Y) + N ln cosh(sh) + ln det(I - tanh(sh) T),
+// Tr(Y' T') = 2^nr <U, T'> - sh Tr T'.
+__global__ void k_entropy_combine(int N, int nr, const double* ld, const double* dots, double* out,
+                                  double sh, const double* ldsh, const double* trT) {
   if (threadIdx.x != 0) return;
   double tot = 0.0;
+  const double lch = sh != 0.0 ? log(cosh(sh)) : 0.0;
   for (int s = 0; s < 2; ++s) {
     double v = -N * 0.69314718055994531 + ldexp(1.0, nr - 1) * ld[s] + ldexp(1.0, nr) * dots[s];
     for (int k = 0; k < nr; ++k) v += ldexp(1.0, nr - 1 - k) * ld[2 * (k + 1) + s];
+    v -= N * lch + ldsh[s];
+    v -= sh * trT[s];
     tot += v;
   }
   out[0] = tot;
+}
+
+// trT[s] = Tr T_s (both spins), fp64 sums
+template <bool BF16>
+__global__ void k_trace2_h(int n, const uint16_t* hi, const uint16_t* lo, double* trT) {
+  __shared__ double sm[1024];
+  for (int s = 0; s < 2; ++s) {
+    double a = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      a += ld_hl_d<BF16>(hi, lo, (size_t)s * n * n + (size_t)i * n + i);
+    sm[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) trT[s] = sm[0];
+    __syncthreads();
+  }
 }
 
 int entropy_mixed(sxl_ctx* c, double* out_dev) {
@@ -1165,11 +1294,23 @@ int entropy_mixed(sxl_ctx* c, double* out_dev) {
     chol_logdet_dev_f32(c, N, c->fscratch, ld + 2 * (k + 1));
   }
   LAUNCH(k_negate_pairs, 1, 64, 0, c->st, nr, ld);
+  // exact chemical-potential shift: ln cosh(y - s) = ln cosh y + ln cosh s + ln(1 - t tau)
+  double* ldsh = c->red + 3180;  // 2: ln det(I - tau T) per spin
+  double* trT = c->red + 3184;   // 2: Tr T' per spin
+  CUDA_TRY(c, cudaMemsetAsync(ldsh, 0, 2 * sizeof(double), c->st));
+  if (c->teff_valid && c->shift_tau != 0.0) {
+    DISPATCH(c, k_hl_to_f32, g, 256, 0, nn2, c->hT[nr].hi, c->hT[nr].lo, c->fscratch,
+             (float)c->shift_tau);
+    chol_logdet_dev_f32(c, N, c->fscratch, ldsh);
+  }
+  const MatH& Tf = final_T_mixed(c);
+  DISPATCH(c, k_trace2_h, 1, 1024, 0, N, Tf.hi, Tf.lo, trT);
   for (int s = 0; s < 2; ++s) {
     DISPATCH(c, k_dot_hl_partial, 128, 256, 0, (long long)nn, c->hU.hi + s * nn, c->hU.lo + s * nn,
-             c->hT[nr].hi + s * nn, c->hT[nr].lo + s * nn, c->red + 2048);
+             Tf.hi + s * nn, Tf.lo + s * nn, c->red + 2048);
     LAUNCH(k_sum_parts, 1, 256, 0, c->st, 128, c->red + 2048, dots + s);
   }
-  LAUNCH(k_entropy_combine, 1, 32, 0, c->st, N, nr, ld, dots, out_dev);
+  const double sh = c->teff_valid ? std::atanh(c->shift_tau) : 0.0;
+  LAUNCH(k_entropy_combine, 1, 32, 0, c->st, N, nr, ld, dots, out_dev, sh, ldsh, trT);
   return SXL_OK;
 }

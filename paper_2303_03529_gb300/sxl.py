@@ -322,6 +322,48 @@ class Context:
         return dict(zip(keys, out.tolist()))
 
 
+def _make_autograd():
+    import torch
+
+    class ShadowEnergy(torch.autograd.Function):
+        """U(R) at constant n (Eq. ShadowULatte) with dU/dR from the library.
+
+        forward(R, n, ctx) runs the density and the force kernel of
+        sxl_forces: the force kernel is the adjoint of the energy with
+        respect to the positions (Tr[D dH0/dR] with the Slater-Koster
+        derivative blocks formed on the fly from the density matrix of the
+        expansion chain, plus the Coulomb and repulsion terms; the spin and
+        entropy terms have no explicit R dependence at constant n and the
+        density is stationary).  backward returns -F times the incoming
+        gradient; no per-orbital derivative tensor is ever stored.
+        """
+
+        @staticmethod
+        def forward(fctx, R, n, ctx):
+            F, en = ctx.forces(R.detach(), n.detach(), energies=True)
+            fctx.save_for_backward(F)
+            return torch.tensor(en["U"], dtype=torch.float64, device=R.device)
+
+        @staticmethod
+        def backward(fctx, gU):
+            (F,) = fctx.saved_tensors
+            return (-F * gU).reshape(F.shape), None, None
+
+    return ShadowEnergy
+
+
+_SHADOW = None
+
+
+def shadow_energy(R, n, ctx):
+    """Differentiable shadow energy: U = shadow_energy(R, n, ctx);
+    U.backward() fills R.grad with dU/dR = -F (eV/Angstrom)."""
+    global _SHADOW
+    if _SHADOW is None:
+        _SHADOW = _make_autograd()
+    return _SHADOW.apply(R, n, ctx)
+
+
 def mixed_gemm_noalloc(n, precision, A, B, E=None, alpha=1.0, beta=0.0, gamma=0.0,
                        sym=False, split=True, stream=None):
     """Allocation-free tensor-core product (sxl_mixed_gemm_noalloc): the caller

@@ -59,6 +59,50 @@ def test_scf_fixed_point():
     assert res["K0"] is not None   # the kernel mixer took over
 
 
+def test_diis_single_entry_is_linear_mixing():
+    rng = np.random.default_rng(3)
+    n, f = rng.standard_normal(7), rng.standard_normal(7)
+    np.testing.assert_allclose(dynamics.diis_update([n], [f], 0.3), n + 0.3 * f, atol=1e-15)
+
+
+def test_diis_two_entries_closed_form():
+    """m = 2: c1 minimizes |c1 f1 + (1 - c1) f2|, c1 = f2.(f2 - f1) / |f1 - f2|^2."""
+    rng = np.random.default_rng(4)
+    n1, n2, f1, f2 = (rng.standard_normal(6) for _ in range(4))
+    c1 = f2 @ (f2 - f1) / ((f1 - f2) @ (f1 - f2))
+    want = c1 * (n1 + 0.1 * f1) + (1 - c1) * (n2 + 0.1 * f2)
+    np.testing.assert_allclose(dynamics.diis_update([n1, n2], [f1, f2], 0.1), want, atol=1e-13)
+
+
+def test_diis_solves_affine_residual_exactly():
+    """For f(n) = b - A n and dim + 1 affinely independent points, sum c_i f_i
+    = 0 is reachable, so the Pulay step lands on A^{-1} b for any mixing."""
+    rng = np.random.default_rng(5)
+    d = 5
+    M = rng.standard_normal((d, d))
+    A = M @ M.T + d * np.eye(d)
+    b = rng.standard_normal(d)
+    ns = [rng.standard_normal(d) for _ in range(d + 1)]
+    fs = [b - A @ x for x in ns]
+    for mix in (0.0, 0.1, 0.7):
+        np.testing.assert_allclose(dynamics.diis_update(ns, fs, mix), np.linalg.solve(A, b),
+                                   atol=1e-10)
+
+
+def test_scf_mixers_reach_the_same_fixed_point():
+    """DIIS and kernel mixing converge to one q[n] = n; the kernel mixer needs
+    the fewest iterations, linear mixing (0.06) is still far from converged
+    after as many iterations as DIIS took (the ordering of Fig. SCF)."""
+    w = wl.fe16()
+    res = {m: dynamics.scf(w.R, w.cell, w.n0, w.params, tol=1e-8, max_iter=400, mixer=m)
+           for m in ("kernel", "diis")}
+    np.testing.assert_allclose(res["diis"]["n"], res["kernel"]["n"], atol=1e-7)
+    assert res["kernel"]["iters"] < res["diis"]["iters"]
+    with pytest.raises(RuntimeError):
+        dynamics.scf(w.R, w.cell, w.n0, w.params, tol=1e-8, max_iter=res["diis"]["iters"],
+                     mixer="linear")
+
+
 def _energy_at(w, R, n):
     d = electronic.density(R, w.cell, n, w.params)
     e_rep = model.repulsive_energy(R, w.cell, w.params)
