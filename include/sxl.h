@@ -81,10 +81,12 @@ typedef struct {
   int    precision;          /* SXL_FP64, SXL_MIXED_FP16 or SXL_MIXED_BF16     */
   int    foe_steps;          /* recursion depth; 0 = choose from spectral bounds */
   double foe_u_max;          /* bound on |eig(U)| that fixes the depth when
-                                foe_steps == 0 (0 = 0.05 for SXL_FP64, 0.2
-                                for the mixed forms)                          */
+                                foe_steps == 0: 0 = 0.05 over the whole
+                                search window for SXL_FP64, 0.5 about each
+                                pass's mu for the mixed forms               */
   int    mu_max_iter;        /* cap on chemical-potential Newton passes (0 = 30) */
-  double mu_tol;             /* |sum Tr D - N_e| tolerance (0 = 1e-10)         */
+  double mu_tol;             /* |sum Tr D - N_e| tolerance (0 = 1e-10 for
+                                SXL_FP64, 1e-6 N_e for the mixed forms)      */
   int    scf_keep_k0;        /* scf_solve: 0 = build the exact K0 = J^{-1} when the
                                 kernel mixer starts, 1 = keep the installed K0 */
 } sxl_params;
@@ -139,7 +141,10 @@ int krylov_kernel_apply(sxl_ctx* ctx, const double* R_dev, const double* n_dev,
 
 /* Stages a7/a8 (Eqs. EqMot, ShadowELatte): density for (R, n), forces at
  * constant n into F_dev (N_at x 3) and, if energies_host is not NULL,
- * [U, E_band, E_coul, E_spin, E_entropy, E_rep] (6 doubles, eV). */
+ * [U, E_band, E_coul, E_spin, E_entropy, E_rep] (6 doubles, eV).  U is the
+ * sum of the five terms plus mu (N_e - sum Tr D), which carries it to the
+ * exact electron count to first order (the search for mu stops at a
+ * tolerance). */
 int forces(sxl_ctx* ctx, const double* R_dev, const double* n_dev,
            double* F_dev, double* energies_host);
 
@@ -187,7 +192,9 @@ int scf_solve(sxl_ctx* ctx, const double* R_dev, double* n_dev, double tol,
  * uses: inputs are rounded to (hi, lo) 16-bit pairs, split = 1 forms the
  * three-product form, split = 0 the hi x hi product only; sym = 1 computes
  * the upper tiles and mirrors them (valid only for a symmetric result).
- * Needs a context created with SXL_MIXED_FP16 or SXL_MIXED_BF16. */
+ * Needs a context created with SXL_MIXED_FP16 or SXL_MIXED_BF16.  Runs in the
+ * context's chain buffers: any density held by the context is discarded
+ * (call sxl_density again before sxl_response or sxl_forces). */
 int sxl_mixed_gemm(sxl_ctx* ctx, const double* A_dev, const double* B_dev, const double* E_dev,
                    double* C_dev, double alpha, double beta, double gamma, int sym, int split);
 

@@ -117,6 +117,8 @@ static int foe_f64(sxl_ctx* c, double mu, double* stats_dev) {
   const int N = c->N, nr = c->nr;
   SXL_TRY(ensure_chain(c, nr));
   c->umax = c->scale * std::max(std::fabs(c->lam_max - mu), std::fabs(mu - c->lam_min));
+  if (!(c->umax <= 1.2))
+    return sxl_fail(c, SXL_E_ARG, "expansion start out of range (|U| > 1.2): raise foe_steps");
   build_u_f64(c, c->H0, c->shift, mu, c->scale, c->U);
   gemm_f64(c, 2, N, c->U, c->U, c->S, 1.0, nullptr, 0.0, 0.0, true);
   gemm_f64(c, 2, N, c->S, c->S, c->Q, 2.0 / 15.0, c->S, -1.0 / 3.0, 1.0, true);
@@ -213,17 +215,26 @@ static int density(sxl_ctx* c, const double* R, const double* n, double mu_guess
   const double Ne = c->p.n_elec_per_atom * c->nat;
   const double kT = c->p.kT;
   double lo = c->lam_min - 40.0 * kT, hi = c->lam_max + 40.0 * kT;
-  if (c->p.foe_steps > 0) {
-    c->nr = c->p.foe_steps;
-  } else {
-    double ymax = 0.5 * c->beta * (hi - lo);
-    // fp64 form: small |U| so that the fifth-order start is exact to ~1e-11
-    // in the effective argument of every state; mixed forms: 4x larger
-    double ut = c->p.foe_u_max > 0 ? c->p.foe_u_max
-                                   : (c->p.precision == SXL_FP64 ? 0.05 : 0.25);
-    c->nr = std::max(4, (int)std::ceil(std::log2(ymax / ut)));
-  }
-  c->scale = c->beta / std::ldexp(1.0, c->nr + 1);
+  const bool mixed = c->p.precision != SXL_FP64;
+  // Depth of the expansion: |U| = |y| / 2^nr <= u_t for every state.
+  // fp64 form: u_t = 0.05 over the whole search window (one depth for all
+  // passes), so the fifth-order start is exact to ~1e-11 in the effective
+  // argument of every state.  Mixed forms: u_t = 0.5 about the pass's own mu.
+  // The start then distorts the argument of states far from mu (which stay
+  // saturated) but not of those near mu (|u| tiny), so q, F and the response
+  // do not see it; the entropy takes the known distortion into account.
+  const double ut = c->p.foe_u_max > 0 ? c->p.foe_u_max : (mixed ? 0.5 : 0.05);
+  const double window = hi - lo;  // lo and hi narrow as the search brackets mu
+  auto set_depth = [&](double m) {
+    if (c->p.foe_steps > 0) {
+      c->nr = c->p.foe_steps;
+    } else {
+      double ymax = mixed ? 0.5 * c->beta * std::max(c->lam_max - m, m - c->lam_min)
+                          : 0.5 * c->beta * window;
+      c->nr = std::max(4, (int)std::ceil(std::log2(ymax / ut)));
+    }
+    c->scale = c->beta / std::ldexp(1.0, c->nr + 1);
+  };
   double mu = std::isfinite(mu_guess) ? mu_guess : 0.5 * (c->lam_min + c->lam_max);
   mu = std::min(std::max(mu, lo), hi);
   const int maxit = c->p.mu_max_iter > 0 ? c->p.mu_max_iter : 30;
@@ -233,8 +244,8 @@ static int density(sxl_ctx* c, const double* R, const double* n, double mu_guess
                                      : (c->p.precision == SXL_FP64 ? 1e-10 : 1e-6 * Ne);
   const bool dbg = getenv("SXL_DEBUG") != nullptr;
   double* stats = c->red + 16;
-  const bool mixed = c->p.precision != SXL_FP64;
   for (int it = 0;; ++it) {
+    set_depth(mu);
     if (mixed) SXL_TRY(foe_mixed(c, mu, stats));
     else SXL_TRY(foe_f64(c, mu, stats));
     SXL_TRY(sync_host(c, stats, 2));
@@ -423,7 +434,11 @@ static int eval_forces(sxl_ctx* c, const double* R, const double* n, double* F, 
     SXL_TRY(sync_host(c, d + 2, 5));
     double band = c->hred[0], coul = c->hred[1], spin = c->hred[2], rep = c->hred[3];
     double ent = c->p.kT * c->hred[4];
-    en[0] = band + coul + spin + ent + rep;
+    // the search stops at |N - N_e| <= tol; d(E_band - kT S)/dmu = mu dN/dmu,
+    // so mu (N_e - N) carries the total to N = N_e to first order (the
+    // remainder is quadratic in the charge error)
+    const double ncorr = c->mu * (c->p.n_elec_per_atom * c->nat - c->last_N);
+    en[0] = band + coul + spin + ent + rep + ncorr;
     en[1] = band; en[2] = coul; en[3] = spin; en[4] = ent; en[5] = rep;
   }
   return SXL_OK;
@@ -459,6 +474,7 @@ int sxl_create(const sxl_params* prm, void* stream, sxl_ctx** out) {
   c->mu = NAN;
   c->mu_prev = NAN;
   c->teff_valid = false;
+  c->apm_ready = false;
   c->shift_tau = 0.0;
   c->fscratch = nullptr;
   c->state_ready = c->evaluated = c->have_density = c->h0_valid = false;
@@ -783,6 +799,8 @@ int sxl_mixed_gemm(sxl_ctx* c, const double* A, const double* B, const double* E
                    double alpha, double beta, double gamma, int sym, int split) {
   if (!c || !A || !B || !C) return SXL_E_ARG;
   if (c->p.precision == SXL_FP64) return sxl_fail(c, SXL_E_STATE, "context is fp64");
+  // the product runs in the density chain's buffers: the density is gone
+  c->have_density = false;
   SXL_TRY(mixed_gemm_test(c, A, B, E, C, alpha, beta, gamma, sym, split));
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   int flag = 0;

@@ -65,6 +65,8 @@ struct sxl_ctx {
   // mixed-precision chain
   MatH hU, hS, hQ, hX0, hX1, hP, hSm, hdTa, hdTb, hG1;
   std::vector<MatH> hT, hY;
+  std::vector<MatH> hAm;  // Y_k - T_{k+1}/2 (response form; hY[k] then holds Y_k + T_{k+1}/2)
+  bool apm_ready;         // hY / hAm hold the response operators of the current chain
   MatH hTeff;             // T_nr after a first-order chemical-potential shift
   MatH hXs;               // (I - tau T_nr)^{-1} of the last exact shift
   float* fscratch;        // 2 N^2 fp32 (entropy factorizations, mixed forms)

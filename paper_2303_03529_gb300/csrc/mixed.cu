@@ -783,6 +783,20 @@ static void axpy_diag_h(sxl_ctx* c, const MatH& out, double a, const MatH& X, do
            out.lo, (float)a, X.hi, X.lo, (float)g);
 }
 
+// A+ = Y + T'/2 (in place of Y), A- = Y - T'/2, element pairs
+template <bool BF16>
+__global__ void k_apm_h(size_t pairs, uint16_t* yhi, uint16_t* ylo, const uint16_t* thi,
+                        const uint16_t* tlo, uint16_t* mhi, uint16_t* mlo) {
+  size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (p >= pairs) return;
+  size_t i = 2 * p;
+  float y0, y1, t0, t1;
+  ld_pair<BF16>(yhi, ylo, i, y0, y1);
+  ld_pair<BF16>(thi, tlo, i, t0, t1);
+  st_pair<BF16>(yhi, ylo, i, y0 + 0.5f * t0, y1 + 0.5f * t1);
+  st_pair<BF16>(mhi, mlo, i, y0 - 0.5f * t0, y1 - 0.5f * t1);
+}
+
 static int halloc(sxl_ctx* c, MatH* m) {
   size_t n = 2 * (size_t)c->N * c->N;
   m->hi = m->lo = nullptr;
@@ -827,8 +841,11 @@ void sxl_mixed_free(sxl_ctx* c) {
   c->fscratch = nullptr;
   for (MatH& m : c->hT) hfree(m);
   for (MatH& m : c->hY) hfree(m);
+  for (MatH& m : c->hAm) hfree(m);
   c->hT.clear();
   c->hY.clear();
+  c->hAm.clear();
+  c->apm_ready = false;
 }
 
 int tc_error_flag(sxl_ctx* c, int* flag) {
@@ -850,6 +867,11 @@ static int ensure_chain_h(sxl_ctx* c, int nr) {
     SXL_TRY(halloc(c, &m));
     c->hY.push_back(m);
   }
+  while ((int)c->hAm.size() < nr) {
+    MatH m;
+    SXL_TRY(halloc(c, &m));
+    c->hAm.push_back(m);
+  }
   return SXL_OK;
 }
 
@@ -861,6 +883,9 @@ int foe_mixed(sxl_ctx* c, double mu, double* stats_dev) {
   SXL_TRY(ensure_chain_h(c, nr));
   const bool split = true;
   c->umax = c->scale * std::max(std::fabs(c->lam_max - mu), std::fabs(mu - c->lam_min));
+  // the start polynomial is monotone with |p(u)| < 1 up to |u| ~ 1.2
+  if (!(c->umax <= 1.2))
+    return sxl_fail(c, SXL_E_ARG, "expansion start out of range (|U| > 1.2): raise foe_steps");
   size_t total = (size_t)N * N;
   DISPATCH(c, k_build_u_h, (unsigned)((total + 255) / 256), 256, 0, c->nat, c->H0, c->shift, mu,
            c->scale, c->hU.hi, c->hU.lo);
@@ -874,6 +899,7 @@ int foe_mixed(sxl_ctx* c, double mu, double* stats_dev) {
   const double tol = 1e-7;
   c->teff_valid = false;
   c->shift_tau = 0.0;
+  c->apm_ready = false;
   c->ns_iters.assign(nr, 0);
   for (int k = 0; k < nr; ++k) {
     const MatH& Sq = c->hSm;
@@ -1002,16 +1028,29 @@ int dmpt_mixed(sxl_ctx* c, const double* du) {
   const MatH* dA = &c->hdTa;
   const MatH* dB = &c->hdTb;
   symcombo_h(c, *dA, 0.0, nullptr, 0.5, &c->hG1, 0.5, du, &c->hQ);
+  // Step k of the chain in sandwich form.  In the common eigenbasis
+  //   dT_{k+1}[a,b] = 2 dT_k[a,b] y_a y_b (1 - t_a t_b),
+  // and 2 y_a y_b (1 - t_a t_b) = y_a (1 - t_a) y_b (1 + t_b) + y_a (1 + t_a) y_b (1 - t_b),
+  // so with A+- = Y_k (I +- T_k) = Y_k +- T_{k+1}/2:
+  //   dT_{k+1} = A- dT A+ + A+ dT A- = A- V^T + V A-,  V = A+ dT.
+  // One full product and one symmetric product over [A- | V][V | A-]^T per
+  // step (the three-product form needs half a product more).
+  if (!c->apm_ready) {
+    const size_t pairs = (size_t)N * N;
+    for (int k = 0; k < nr; ++k)
+      DISPATCH(c, k_apm_h, (unsigned)((pairs + 255) / 256), 256, 0, pairs, c->hY[k].hi,
+               c->hY[k].lo, c->hT[k + 1].hi, c->hT[k + 1].lo, c->hAm[k].hi, c->hAm[k].lo);
+    c->apm_ready = true;
+  }
   for (int k = 0; k < nr; ++k) {
+    SXL_TRY(gemm_tc(c, c->hY[k], *dA, c->hG1, 1.f, nullptr, 0.f, 0.f, false, split));
     if (split) {
-      SXL_TRY(gemm_tc(c, c->hT[k], *dA, c->hP, 1.f, nullptr, 0.f, 0.f, false, split));
-      symcombo_h(c, c->hSm, 0.0, nullptr, 1.0, &c->hP, 0.0, nullptr, nullptr);
+      SXL_TRY(gemm_tc(c, c->hAm[k], c->hG1, c->hP, 1.f, nullptr, 0.f, 0.f, false, split));
+      symcombo_h(c, *dB, 0.0, nullptr, 1.0, &c->hP, 0.0, nullptr, nullptr);
     } else {
-      // S = T dT + dT T in one symmetric product over [T | dT] [dT | T]^T
-      SXL_TRY(gemm_tc_dual(c, c->hT[k], *dA, *dA, c->hT[k], c->hSm, 1.f, nullptr, 0.f, 0.f, true));
+      SXL_TRY(gemm_tc_dual(c, c->hAm[k], c->hG1, c->hG1, c->hAm[k], *dB, 1.f, nullptr, 0.f, 0.f,
+                           true));
     }
-    SXL_TRY(gemm_tc(c, c->hT[k + 1], c->hSm, c->hG1, -0.5f, dA, 1.f, 0.f, false, split));
-    SXL_TRY(gemm_tc(c, c->hG1, c->hY[k], *dB, 2.f, nullptr, 0.f, 0.f, true, split));
     std::swap(dA, dB);
   }
   if (c->teff_valid && c->shift_tau != 0.0) {
@@ -1236,12 +1275,14 @@ __global__ void k_dot_hl_partial(long long len, const uint16_t* ah, const uint16
 // Tr ln cosh(Y') = Tr ln cosh(Y) + N ln cosh(sh) + ln det(I - tanh(sh) T),
 // Tr(Y' T') = 2^nr <U, T'> - sh Tr T'.
 __global__ void k_entropy_combine(int N, int nr, const double* ld, const double* dots, double* out,
-                                  double sh, const double* ldsh, const double* trT) {
+                                  double sh, const double* ldsh, const double* trT,
+                                  const double* corr, double a3) {
   if (threadIdx.x != 0) return;
   double tot = 0.0;
   const double lch = sh != 0.0 ? log(cosh(sh)) : 0.0;
   for (int s = 0; s < 2; ++s) {
-    double v = -N * 0.69314718055994531 + ldexp(1.0, nr - 1) * ld[s] + ldexp(1.0, nr) * dots[s];
+    double v = -N * 0.69314718055994531 + ldexp(1.0, nr - 1) * ld[s] +
+               ldexp(1.0, nr) * (dots[s] + a3 * corr[s]);
     for (int k = 0; k < nr; ++k) v += ldexp(1.0, nr - 1 - k) * ld[2 * (k + 1) + s];
     v -= N * lch + ldsh[s];
     v -= sh * trT[s];
@@ -1310,7 +1351,33 @@ int entropy_mixed(sxl_ctx* c, double* out_dev) {
              Tf.hi + s * nn, Tf.lo + s * nn, c->red + 2048);
     LAUNCH(k_sum_parts, 1, 256, 0, c->st, 128, c->red + 2048, dots + s);
   }
+  // The fifth-order start is tanh of artanh(p(U)) = U + delta(U), not of U:
+  // the chain's argument is 2^nr (U + delta(U)), and Tr(Y T) takes the term
+  // 2^nr <delta(U), T> with delta(u) = u^7 (17/315 + 13 u^2/405 + 37 u^4/7425
+  // + 2 u^6/5265) (relative error < 3e-4 for |u| <= 0.5).  In S' = U^2 / a,
+  // a = u_max^2 (spectrum in [0, 1]): delta(U) = a^3 U S'^3 g(S').
+  double* corr = c->red + 3176;  // 2
+  CUDA_TRY(c, cudaMemsetAsync(corr, 0, 2 * sizeof(double), c->st));
+  double a3 = 0.0;
+  if (c->umax > 0.02) {
+    const double a = c->umax * c->umax;
+    a3 = a * a * a;
+    const double d7 = 17.0 / 315.0, d9 = 13.0 / 405.0 * a, d11 = 37.0 / 7425.0 * a * a,
+                 d13 = 2.0 / 5265.0 * a * a * a;
+    axpy_diag_h(c, c->hX0, 1.0 / a, c->hS, 0.0);                                    // S'
+    SXL_TRY(gemm_tc(c, c->hX0, c->hX0, c->hX1, 1.f, nullptr, 0.f, 0.f, true, false));  // S'^2
+    axpy_diag_h(c, c->hP, d13, c->hX0, d11);
+    SXL_TRY(gemm_tc(c, c->hX1, c->hP, c->hG1, 1.f, &c->hX0, (float)d9, (float)d7, true, false));
+    SXL_TRY(gemm_tc(c, c->hX1, c->hX0, c->hP, 1.f, nullptr, 0.f, 0.f, true, false));   // S'^3
+    SXL_TRY(gemm_tc(c, c->hP, c->hG1, c->hX1, 1.f, nullptr, 0.f, 0.f, true, false));   // S'^3 g
+    SXL_TRY(gemm_tc(c, c->hU, c->hX1, c->hP, 1.f, nullptr, 0.f, 0.f, true, false));    // U S'^3 g
+    for (int s = 0; s < 2; ++s) {
+      DISPATCH(c, k_dot_hl_partial, 128, 256, 0, (long long)nn, c->hP.hi + s * nn,
+               c->hP.lo + s * nn, Tf.hi + s * nn, Tf.lo + s * nn, c->red + 2048);
+      LAUNCH(k_sum_parts, 1, 256, 0, c->st, 128, c->red + 2048, corr + s);
+    }
+  }
   const double sh = c->teff_valid ? std::atanh(c->shift_tau) : 0.0;
-  LAUNCH(k_entropy_combine, 1, 32, 0, c->st, N, nr, ld, dots, out_dev, sh, ldsh, trT);
+  LAUNCH(k_entropy_combine, 1, 32, 0, c->st, N, nr, ld, dots, out_dev, sh, ldsh, trT, corr, a3);
   return SXL_OK;
 }
