@@ -468,6 +468,8 @@ int sxl_create(const sxl_params* prm, void* stream, sxl_ctx** out) {
   c->st = (cudaStream_t)stream;
   c->nat = p.n_atoms;
   c->N = NORB * p.n_atoms;
+  c->Np = c->N;
+  c->dup = nullptr;
   c->n2 = 2 * p.n_atoms;
   c->beta = 1.0 / p.kT;
   c->hist_head = 0;

@@ -27,7 +27,7 @@ extern unsigned long long g_sxl_launches;
 #define LO_SHIFT 12
 
 struct MatH {
-  uint16_t* hi;  // fp16 or bf16 bits, row-major N x N per spin, spin stride N*N
+  uint16_t* hi;  // fp16 or bf16 bits, row-major Np x Np per spin, spin stride Np*Np
   uint16_t* lo;
 };
 
@@ -62,14 +62,18 @@ struct sxl_ctx {
   double *U, *S, *Q, *X0, *X1, *P, *Sm, *dTa, *dTb, *G1;
   std::vector<double*> T, Y;
   std::vector<int> ns_iters;  // Newton-Schulz iterations used at each step
-  // mixed-precision chain
+  // mixed-precision chain, on the dimension Np = N rounded up to 64: the
+  // padding orbitals form a decoupled diagonal block at the upper spectral
+  // bound (empty states)
+  int Np;
+  double* dup;            // 2 x Np perturbation (zero on the padding)
   MatH hU, hS, hQ, hX0, hX1, hP, hSm, hdTa, hdTb, hG1;
   std::vector<MatH> hT, hY;
   std::vector<MatH> hAm;  // Y_k - T_{k+1}/2 (response form; hY[k] then holds Y_k + T_{k+1}/2)
   bool apm_ready;         // hY / hAm hold the response operators of the current chain
   MatH hTeff;             // T_nr after a first-order chemical-potential shift
   MatH hXs;               // (I - tau T_nr)^{-1} of the last exact shift
-  float* fscratch;        // 2 N^2 fp32 (entropy factorizations, mixed forms)
+  float* fscratch;        // 2 Np^2 fp32 (entropy factorizations, mixed forms)
   bool teff_valid;        // hTeff (not hT[nr]) holds the final density
   double shift_tau;       // tanh(beta dmu / 2) of the exact shift in hTeff (0: none)
   double mu_prev;         // chemical potential of the previous MD step (NaN: none)

@@ -511,7 +511,7 @@ static int launch_tc(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a) {
 int gemm_tc(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C, float alpha,
             const MatH* E, float beta, float gamma, bool sym, bool split) {
   const bool bf16 = c->p.precision == SXL_MIXED_BF16;
-  const int n = c->N;
+  const int n = c->Np;
   // K-block per product form (measured at n = 9216): split products run best
   // with 32-wide blocks (four 48 KB stages), plain ones with 64-wide blocks
   // (four 48 KB stages as well).  SXL_TC_BK=32 or 64 forces one width.
@@ -567,7 +567,7 @@ int gemm_tc(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C, float alpha
 int gemm_tc_dual(sxl_ctx* c, const MatH& A1, const MatH& B1, const MatH& A2, const MatH& B2,
                  const MatH& C, float alpha, const MatH* E, float beta, float gamma, bool sym) {
   const bool bf16 = c->p.precision == SXL_MIXED_BF16;
-  const int n = c->N, bk = 64, mt = 2;
+  const int n = c->Np, bk = 64, mt = 2;
   CUtensorMap maps[4];
   SXL_TRY(make_map(c, &maps[0], A1.hi, n, TC_BM * mt, bf16, bk));
   SXL_TRY(make_map(c, &maps[1], A2.hi, n, TC_BM * mt, bf16, bk));
@@ -596,33 +596,43 @@ int gemm_tc_dual(sxl_ctx* c, const MatH& A1, const MatH& B1, const MatH& A2, con
 // ---------------------------------------------------------------------------
 // elementwise kernels on (hi, lo) matrices
 template <bool BF16>
-__global__ void k_build_u_h(int nat, const double* __restrict__ H0, const double* __restrict__ shift,
-                            double mu, double scale, uint16_t* hi, uint16_t* lo) {
+// U on the chain dimension np >= N: the padding block is diagonal at the
+// upper spectral bound e_pad (decoupled, empty states; see foe_mixed)
+__global__ void k_build_u_h(int nat, int np, const double* __restrict__ H0,
+                            const double* __restrict__ shift, double mu, double scale, double e_pad,
+                            uint16_t* hi, uint16_t* lo) {
   const int N = nat * NORB;
-  size_t total = (size_t)N * N;
+  size_t total = (size_t)np * np;
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i >= total) return;
-  int r = (int)(i / N), col = (int)(i % N);
-  double h = H0[i];
-  double u0 = scale * h, u1 = u0;
-  if (r == col) {
-    u0 = scale * (h + shift[r / NORB] - mu);
-    u1 = scale * (h + shift[nat + r / NORB] - mu);
+  int r = (int)(i / np), col = (int)(i % np);
+  double u0 = 0.0, u1 = 0.0;
+  if (r < N && col < N) {
+    double h = H0[(size_t)r * N + col];
+    u0 = u1 = scale * h;
+    if (r == col) {
+      u0 = scale * (h + shift[r / NORB] - mu);
+      u1 = scale * (h + shift[nat + r / NORB] - mu);
+    }
+  } else if (r == col) {
+    u0 = u1 = scale * (e_pad - mu);
   }
   st_hl<BF16>(hi, lo, i, (float)u0);
   st_hl<BF16>(hi, lo, total + i, (float)u1);
 }
 
 template <bool BF16>
-__global__ void k_rowstats_h(int n, int rows, const uint16_t* hi, const uint16_t* lo, double* diag,
+__global__ void k_rowstats_h(int np, int n, const uint16_t* hi, const uint16_t* lo, double* diag,
                              double* rowsq) {
+  // rows of the n real orbitals of both spins (matrices np x np); outputs
+  // indexed by spin * n + row
   int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   int lane = threadIdx.x & 31;
-  if (row >= rows) return;
+  if (row >= 2 * n) return;
   int b = row / n, i = row % n;
-  size_t base = (size_t)b * n * n + (size_t)i * n;
+  size_t base = (size_t)b * np * np + (size_t)i * np;
   double s = 0.0;
-  for (int j = lane; j < n; j += 32) {
+  for (int j = lane; j < np; j += 32) {
     double t = ld_hl_d<BF16>(hi, lo, base + j);
     s += t * t;
   }
@@ -635,12 +645,14 @@ __global__ void k_rowstats_h(int n, int rows, const uint16_t* hi, const uint16_t
 
 // out[0] = sum_ij H0_ij T_ij for spin s (deterministic two-stage)
 template <bool BF16>
-__global__ void k_dot_h_partial(long long len, const double* __restrict__ H0, const uint16_t* hi,
+__global__ void k_dot_h_partial(int n, int np, const double* __restrict__ H0, const uint16_t* hi,
                                 const uint16_t* lo, double* part) {
+  // sum over the n x n real block of H0 (ld n) and T (ld np)
   __shared__ double sm[256];
   double s = 0.0;
+  const long long len = (long long)n * n;
   for (long long i = blockIdx.x * 256LL + threadIdx.x; i < len; i += 256LL * gridDim.x)
-    s += H0[i] * ld_hl_d<BF16>(hi, lo, i);
+    s += H0[i] * ld_hl_d<BF16>(hi, lo, (size_t)(i / n) * np + (size_t)(i % n));
   sm[threadIdx.x] = s;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
@@ -662,19 +674,15 @@ __global__ void k_sum_parts(int np, const double* part, double* out) {
 }
 
 template <bool BF16>
-__global__ void k_diag2_h(int n, const uint16_t* hi, const uint16_t* lo, double* out) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 2 * n) return;
-  int s = i / n, r = i % n;
-  out[i] = ld_hl_d<BF16>(hi, lo, (size_t)s * n * n + (size_t)r * n + r);
-}
-
-template <bool BF16>
-__global__ void k_d_from_t_h(size_t nn, const uint16_t* hi, const uint16_t* lo, double* D, int N) {
+__global__ void k_d_from_t_h(size_t nn, const uint16_t* hi, const uint16_t* lo, double* D, int N,
+                             int np) {
+  // nn = 2 N^2 outputs (both spins, ld N) from T (ld np)
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i >= nn) return;
-  size_t e = i % ((size_t)N * N);
-  D[i] = ((e / N == e % N) ? 0.5 : 0.0) - 0.5 * ld_hl_d<BF16>(hi, lo, i);
+  const size_t sp = i / ((size_t)N * N), e = i % ((size_t)N * N);
+  const size_t r = e / N, col = e % N;
+  D[i] = ((r == col) ? 0.5 : 0.0) -
+         0.5 * ld_hl_d<BF16>(hi, lo, sp * np * np + r * np + col);
 }
 
 // ---------------------------------------------------------------------------
@@ -754,7 +762,7 @@ __global__ void k_symcombo2_h(int n, uint16_t* ohi, uint16_t* olo, float a, cons
 
 static void symcombo_h(sxl_ctx* c, const MatH& out, double a, const MatH* X, double b,
                        const MatH* Y, double cc, const double* w, const MatH* Z) {
-  int n = c->N;  // the mixed forms require n % 64 == 0
+  int n = c->Np;  // the chain dimension is a multiple of 64
   dim3 grid(n / 64, n / 32, 2), block(32, 8);
   DISPATCH(c, k_symcombo2_h, grid, block, 0, n, out.hi, out.lo, (float)a, X ? X->hi : nullptr,
            X ? X->lo : nullptr, (float)b, Y ? Y->hi : nullptr, Y ? Y->lo : nullptr, (float)cc, w,
@@ -778,9 +786,34 @@ __global__ void k_axpy_diag2_h(size_t pairs, int n, uint16_t* ohi, uint16_t* olo
 }
 
 static void axpy_diag_h(sxl_ctx* c, const MatH& out, double a, const MatH& X, double g) {
-  size_t pairs = (size_t)c->N * c->N;  // 2 spins x N^2 / 2
-  DISPATCH(c, k_axpy_diag2_h, (unsigned)((pairs + 255) / 256), 256, 0, pairs, c->N, out.hi,
+  size_t pairs = (size_t)c->Np * c->Np;  // 2 spins x Np^2 / 2
+  DISPATCH(c, k_axpy_diag2_h, (unsigned)((pairs + 255) / 256), 256, 0, pairs, c->Np, out.hi,
            out.lo, (float)a, X.hi, X.lo, (float)g);
+}
+
+// out[s n + r] = scale sum_j A[s][r][j] B[s][r][j] for the n real rows of
+// both spins (one warp per row; matrices np x np), i.e. diag(A B^T)
+template <bool BF16>
+__global__ void k_rowdot2_h(int np, int n, const uint16_t* ahi, const uint16_t* alo,
+                            const uint16_t* bhi, const uint16_t* blo, double scale, double* out) {
+  int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  int lane = threadIdx.x & 31;
+  if (row >= 2 * n) return;
+  int b = row / n, i = row % n;
+  size_t base = (size_t)b * np * np + (size_t)i * np;
+  double acc = 0.0;
+  for (int j = lane; j < np; j += 32)
+    acc += (double)ld_hl<BF16>(ahi, alo, base + j) * (double)ld_hl<BF16>(bhi, blo, base + j);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) out[row] = scale * acc;
+}
+
+// w (2 x n) -> wp (2 x np), zero on the padding
+__global__ void k_pad_vec(int n, int np, const double* w, double* wp) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * np) return;
+  int s = i / np, r = i % np;
+  wp[i] = r < n ? w[(size_t)s * n + r] : 0.0;
 }
 
 // A+ = Y + T'/2 (in place of Y), A- = Y - T'/2, element pairs
@@ -798,7 +831,7 @@ __global__ void k_apm_h(size_t pairs, uint16_t* yhi, uint16_t* ylo, const uint16
 }
 
 static int halloc(sxl_ctx* c, MatH* m) {
-  size_t n = 2 * (size_t)c->N * c->N;
+  size_t n = 2 * (size_t)c->Np * c->Np;
   m->hi = m->lo = nullptr;
   if (cudaMalloc((void**)&m->hi, n * 2) != cudaSuccess ||
       cudaMalloc((void**)&m->lo, n * 2) != cudaSuccess)
@@ -814,8 +847,8 @@ static void hfree(MatH& m) {
 }
 
 int sxl_mixed_supported(sxl_ctx* c) {
-  if (c->N % 64 != 0)
-    return sxl_fail(c, SXL_E_ARG, "mixed precision needs 9 N_at to be a multiple of 64");
+  // the chain runs on Np = N rounded up to 64 (tile and TMA granularity)
+  c->Np = (c->N + 63) / 64 * 64;
   int dev = 0;
   CUDA_TRY(c, cudaGetDevice(&dev));
   cudaDeviceProp prop;
@@ -829,6 +862,7 @@ int sxl_mixed_supported(sxl_ctx* c) {
   MatH* ms[] = {&c->hU, &c->hS, &c->hQ, &c->hX0, &c->hX1, &c->hP, &c->hSm, &c->hdTa, &c->hdTb, &c->hG1,
                 &c->hTeff, &c->hXs};
   for (MatH* m : ms) SXL_TRY(halloc(c, m));
+  CUDA_TRY(c, cudaMalloc((void**)&c->dup, 2 * (size_t)c->Np * sizeof(double)));
   c->teff_valid = false;
   return SXL_OK;
 }
@@ -839,6 +873,8 @@ void sxl_mixed_free(sxl_ctx* c) {
   for (MatH* m : ms) hfree(*m);
   if (c->fscratch) cudaFree(c->fscratch);
   c->fscratch = nullptr;
+  if (c->dup) cudaFree(c->dup);
+  c->dup = nullptr;
   for (MatH& m : c->hT) hfree(m);
   for (MatH& m : c->hY) hfree(m);
   for (MatH& m : c->hAm) hfree(m);
@@ -879,16 +915,18 @@ static double tanh5(double u) { return u - u * u * u / 3.0 + 2.0 * std::pow(u, 5
 
 // Same recursion as the fp64 form (see api.cu), on tensor cores.
 int foe_mixed(sxl_ctx* c, double mu, double* stats_dev) {
-  const int N = c->N, nr = c->nr;
+  const int N = c->N, Np = c->Np, nr = c->nr;
   SXL_TRY(ensure_chain_h(c, nr));
   const bool split = true;
   c->umax = c->scale * std::max(std::fabs(c->lam_max - mu), std::fabs(mu - c->lam_min));
   // the start polynomial is monotone with |p(u)| < 1 up to |u| ~ 1.2
   if (!(c->umax <= 1.2))
     return sxl_fail(c, SXL_E_ARG, "expansion start out of range (|U| > 1.2): raise foe_steps");
-  size_t total = (size_t)N * N;
-  DISPATCH(c, k_build_u_h, (unsigned)((total + 255) / 256), 256, 0, c->nat, c->H0, c->shift, mu,
-           c->scale, c->hU.hi, c->hU.lo);
+  // padding orbitals (Np > N) sit at the upper spectral bound: |u| <= umax,
+  // and with mu inside the spectrum they stay empty (f ~ exp(-beta (lam_max - mu)))
+  size_t total = (size_t)Np * Np;
+  DISPATCH(c, k_build_u_h, (unsigned)((total + 255) / 256), 256, 0, c->nat, Np, c->H0, c->shift, mu,
+           c->scale, c->lam_max, c->hU.hi, c->hU.lo);
   SXL_TRY(gemm_tc(c, c->hU, c->hU, c->hS, 1.f, nullptr, 0.f, 0.f, true, split));
   SXL_TRY(gemm_tc(c, c->hS, c->hS, c->hQ, (float)(2.0 / 15.0), &c->hS, (float)(-1.0 / 3.0), 1.f,
                   true, split));
@@ -933,7 +971,7 @@ int foe_mixed(sxl_ctx* c, double mu, double* stats_dev) {
     t = 2.0 * t / (1.0 + t * t);
   }
   int wpb = 8, rows = 2 * N;
-  DISPATCH(c, k_rowstats_h, (rows + wpb - 1) / wpb, 32 * wpb, 0, N, rows, c->hT[nr].hi,
+  DISPATCH(c, k_rowstats_h, (rows + wpb - 1) / wpb, 32 * wpb, 0, Np, N, c->hT[nr].hi,
            c->hT[nr].lo, c->diagT, c->rowsq);
   small_kernels_density(c, c->q, stats_dev);
   return SXL_OK;
@@ -977,7 +1015,7 @@ int mu_shift_exact_mixed(sxl_ctx* c, double dmu, double* stats_dev) {
   c->teff_valid = true;
   c->shift_tau = tau;
   int wpb = 8, rows = 2 * N;
-  DISPATCH(c, k_rowstats_h, (rows + wpb - 1) / wpb, 32 * wpb, 0, N, rows, c->hTeff.hi,
+  DISPATCH(c, k_rowstats_h, (rows + wpb - 1) / wpb, 32 * wpb, 0, c->Np, N, c->hTeff.hi,
            c->hTeff.lo, c->diagT, c->rowsq);
   small_kernels_density(c, c->q, stats_dev);
   return SXL_OK;
@@ -1001,14 +1039,14 @@ int mu_shift_mixed(sxl_ctx* c, double dmu, double* stats_dev) {
   }
   c->teff_valid = true;
   int wpb = 8, rows = 2 * N;
-  DISPATCH(c, k_rowstats_h, (rows + wpb - 1) / wpb, 32 * wpb, 0, N, rows, c->hTeff.hi,
+  DISPATCH(c, k_rowstats_h, (rows + wpb - 1) / wpb, 32 * wpb, 0, c->Np, N, c->hTeff.hi,
            c->hTeff.lo, c->diagT, c->rowsq);
   small_kernels_density(c, c->q, stats_dev);
   return SXL_OK;
 }
 
-int dmpt_mixed(sxl_ctx* c, const double* du) {
-  const int N = c->N, nr = c->nr;
+int dmpt_mixed(sxl_ctx* c, const double* du_real) {
+  const int N = c->N, Np = c->Np, nr = c->nr;
   // The response products run on the hi parts alone (fp16/bf16 operands,
   // fp32 accumulation; one product per k step): the relative error of q_v is
   // about 7e-4 (fp16) / 5e-3 (bf16) against 2e-5 / 1e-4 in the split form,
@@ -1020,6 +1058,9 @@ int dmpt_mixed(sxl_ctx* c, const double* du) {
     use_split = (e && atoi(e) == 1) ? 1 : 0;
   }
   const bool split = use_split == 1;
+  // the perturbation on the chain dimension (zero on the padding)
+  double* du = c->dup;
+  LAUNCH(k_pad_vec, (2 * Np + 255) / 256, 256, 0, c->st, N, Np, du_real, du);
   const MatH& dS = c->hSm;
   symcombo_h(c, dS, 0.0, nullptr, 0.0, nullptr, 1.0, du, &c->hU);
   SXL_TRY(gemm_tc(c, dS, c->hS, c->hG1, 1.f, nullptr, 0.f, 0.f, false, split));
@@ -1036,14 +1077,24 @@ int dmpt_mixed(sxl_ctx* c, const double* du) {
   // One full product and one symmetric product over [A- | V][V | A-]^T per
   // step (the three-product form needs half a product more).
   if (!c->apm_ready) {
-    const size_t pairs = (size_t)N * N;
+    const size_t pairs = (size_t)Np * Np;
     for (int k = 0; k < nr; ++k)
       DISPATCH(c, k_apm_h, (unsigned)((pairs + 255) / 256), 256, 0, pairs, c->hY[k].hi,
                c->hY[k].lo, c->hT[k + 1].hi, c->hT[k + 1].lo, c->hAm[k].hi, c->hAm[k].lo);
     c->apm_ready = true;
   }
+  // Only diag(dT_nr) is needed (q_v): the last step ends in row dots,
+  // diag(A- V^T + V A-) = 2 rowdot(A-, V), and with an exact shift the map
+  // (1 - tau^2) X dT X ends in diag(X dT X) = rowdot(X dT, X).
+  const bool shifted = c->teff_valid && c->shift_tau != 0.0;
+  const int wpb = 8;
   for (int k = 0; k < nr; ++k) {
     SXL_TRY(gemm_tc(c, c->hY[k], *dA, c->hG1, 1.f, nullptr, 0.f, 0.f, false, split));
+    if (k == nr - 1 && !shifted) {
+      DISPATCH(c, k_rowdot2_h, (2 * N + wpb - 1) / wpb, 32 * wpb, 0, Np, N, c->hAm[k].hi,
+               c->hAm[k].lo, c->hG1.hi, c->hG1.lo, 2.0, c->diagT + 2 * N);
+      return SXL_OK;
+    }
     if (split) {
       SXL_TRY(gemm_tc(c, c->hAm[k], c->hG1, c->hP, 1.f, nullptr, 0.f, 0.f, false, split));
       symcombo_h(c, *dB, 0.0, nullptr, 1.0, &c->hP, 0.0, nullptr, nullptr);
@@ -1053,22 +1104,18 @@ int dmpt_mixed(sxl_ctx* c, const double* du) {
     }
     std::swap(dA, dB);
   }
-  if (c->teff_valid && c->shift_tau != 0.0) {
-    // the final T was shifted exactly (tanh addition): the same map carries
-    // the response, dT' = (1 - tau^2) X dT X with X = (I - tau T)^{-1}
-    const float f = (float)(1.0 - c->shift_tau * c->shift_tau);
-    SXL_TRY(gemm_tc(c, c->hXs, *dA, c->hG1, 1.f, nullptr, 0.f, 0.f, false, split));
-    SXL_TRY(gemm_tc(c, c->hG1, c->hXs, *dB, f, nullptr, 0.f, 0.f, true, split));
-    std::swap(dA, dB);
-  }
-  DISPATCH(c, k_diag2_h, (2 * N + 255) / 256, 256, 0, N, dA->hi, dA->lo, c->diagT + 2 * N);
+  // the final T was shifted exactly (tanh addition): the same map carries
+  // the response, dT' = (1 - tau^2) X dT X with X = (I - tau T)^{-1}
+  SXL_TRY(gemm_tc(c, c->hXs, *dA, c->hG1, 1.f, nullptr, 0.f, 0.f, false, split));
+  DISPATCH(c, k_rowdot2_h, (2 * N + wpb - 1) / wpb, 32 * wpb, 0, Np, N, c->hG1.hi, c->hG1.lo,
+           c->hXs.hi, c->hXs.lo, 1.0 - c->shift_tau * c->shift_tau, c->diagT + 2 * N);
   return SXL_OK;
 }
 
 void dot_h0_t_mixed(sxl_ctx* c, int spin, double* out) {
-  const size_t nn = (size_t)c->N * c->N;
+  const size_t nn = (size_t)c->Np * c->Np;
   const MatH& T = final_T_mixed(c);
-  DISPATCH(c, k_dot_h_partial, 128, 256, 0, (long long)nn, c->H0, T.hi + spin * nn, T.lo + spin * nn,
+  DISPATCH(c, k_dot_h_partial, 128, 256, 0, c->N, c->Np, c->H0, T.hi + spin * nn, T.lo + spin * nn,
            c->red + 2048);
   LAUNCH(k_sum_parts, 1, 256, 0, c->st, 128, c->red + 2048, out);
 }
@@ -1076,7 +1123,7 @@ void dot_h0_t_mixed(sxl_ctx* c, int spin, double* out) {
 void density_matrix_mixed(sxl_ctx* c, double* D) {
   size_t nn = 2 * (size_t)c->N * c->N;
   const MatH& T = final_T_mixed(c);
-  DISPATCH(c, k_d_from_t_h, (unsigned)((nn + 255) / 256), 256, 0, nn, T.hi, T.lo, D, c->N);
+  DISPATCH(c, k_d_from_t_h, (unsigned)((nn + 255) / 256), 256, 0, nn, T.hi, T.lo, D, c->N, c->Np);
 }
 
 // standalone product for tests: C = A B^T on (hi, lo) inputs built from fp64
@@ -1093,6 +1140,8 @@ __global__ void k_join_f64(size_t n, const uint16_t* hi, const uint16_t* lo, dou
 
 int mixed_gemm_test(sxl_ctx* c, const double* A, const double* B, const double* E, double* C,
                     double alpha, double beta, double gamma, int sym, int split) {
+  if (c->Np != c->N)
+    return sxl_fail(c, SXL_E_ARG, "the diagnostic product needs 9 N_at to be a multiple of 64");
   size_t nn = 2 * (size_t)c->N * c->N;
   unsigned g = (unsigned)((nn + 255) / 256);
   DISPATCH(c, k_split_f64, g, 256, 0, nn, A, c->hU.hi, c->hU.lo);
@@ -1311,7 +1360,9 @@ __global__ void k_trace2_h(int n, const uint16_t* hi, const uint16_t* lo, double
 }
 
 int entropy_mixed(sxl_ctx* c, double* out_dev) {
-  const int N = c->N, nr = c->nr;
+  // every term runs over all Np states of the chain; the padding states are
+  // saturated (t = 1) and contribute -ln(1 + e^{-2y}) ~ 0 in total
+  const int N = c->Np, nr = c->nr;
   const size_t nn = (size_t)N * N, nn2 = 2 * nn;
   if (!c->fscratch) {
     if (cudaMalloc((void**)&c->fscratch, nn2 * sizeof(float)) != cudaSuccess)

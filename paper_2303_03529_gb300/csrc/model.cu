@@ -261,14 +261,16 @@ void launch_spin_shift(sxl_ctx* c, const double* n, double* out) {
 //   a = 2q - n, b = n (per-atom totals).
 // The sums run in a fixed order, so the result is deterministic.
 template <class TS>
-__device__ inline double tsum_at(const TS& ts, size_t idx);
+__device__ inline double tsum_at(const TS& ts, size_t r, size_t col);
 
 struct TsumF64 {
-  const double* T;   // 2 x N x N
-  size_t nn;
+  const double* T;   // 2 x ld x ld
+  size_t nn;         // ld^2 (spin stride)
+  size_t ld;
 };
 template <>
-__device__ inline double tsum_at<TsumF64>(const TsumF64& ts, size_t idx) {
+__device__ inline double tsum_at<TsumF64>(const TsumF64& ts, size_t r, size_t col) {
+  const size_t idx = r * ts.ld + col;
   return ts.T[idx] + ts.T[ts.nn + idx];
 }
 
@@ -276,14 +278,17 @@ template <bool BF16>
 struct TsumH {
   const uint16_t* hi;
   const uint16_t* lo;
-  size_t nn;
+  size_t nn;         // ld^2 (spin stride)
+  size_t ld;         // chain dimension Np
 };
 template <>
-__device__ inline double tsum_at<TsumH<false>>(const TsumH<false>& ts, size_t idx) {
+__device__ inline double tsum_at<TsumH<false>>(const TsumH<false>& ts, size_t r, size_t col) {
+  const size_t idx = r * ts.ld + col;
   return hl_value<false>(ts.hi, ts.lo, idx) + hl_value<false>(ts.hi, ts.lo, ts.nn + idx);
 }
 template <>
-__device__ inline double tsum_at<TsumH<true>>(const TsumH<true>& ts, size_t idx) {
+__device__ inline double tsum_at<TsumH<true>>(const TsumH<true>& ts, size_t r, size_t col) {
+  const size_t idx = r * ts.ld + col;
   return hl_value<true>(ts.hi, ts.lo, idx) + hl_value<true>(ts.hi, ts.lo, ts.nn + idx);
 }
 
@@ -295,7 +300,6 @@ __global__ void __launch_bounds__(256) k_forces(int nat, const double* __restric
                                                 double* __restrict__ F,
                                                 double* __restrict__ erep) {
   const int K = blockIdx.x;
-  const int N = nat * NORB;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
   double fx = 0.0, fy = 0.0, fz = 0.0, er = 0.0;
@@ -324,7 +328,7 @@ __global__ void __launch_bounds__(256) k_forces(int nat, const double* __restric
       for (int e = lane; e < NORB * NORB; e += 32) {
         int a = e / NORB, b = e % NORB;
         Dual3 E = sk_elem<Dual3>(a, b, l, m, nn, V);
-        double dsum = -0.5 * tsum_at<TS>(ts, (size_t)(NORB * K + a) * N + NORB * J + b);
+        double dsum = -0.5 * tsum_at<TS>(ts, (size_t)(NORB * K + a), (size_t)(NORB * J + b));
         fx += 2.0 * dsum * E.g0;
         fy += 2.0 * dsum * E.g1;
         fz += 2.0 * dsum * E.g2;
@@ -370,17 +374,17 @@ __global__ void __launch_bounds__(256) k_forces(int nat, const double* __restric
 void launch_forces(sxl_ctx* c, const double* R, const double* n, const double* qspin,
                    double* F, double* erep_atom) {
   ModelConst mc = model_const(c->p);
-  const size_t nn = (size_t)c->N * c->N;
+  const size_t nn = (size_t)c->N * c->N, npp = (size_t)c->Np * c->Np;
   if (c->p.precision == SXL_FP64) {
-    TsumF64 ts{c->T[c->nr], nn};
+    TsumF64 ts{c->T[c->nr], nn, (size_t)c->N};
     LAUNCH(k_forces<TsumF64>, c->nat, 256, 0, c->st, c->nat, R, mc, ts, n, qspin, F, erep_atom);
   } else if (c->p.precision == SXL_MIXED_BF16) {
     const MatH& T = final_T_mixed(c);
-    TsumH<true> ts{T.hi, T.lo, nn};
+    TsumH<true> ts{T.hi, T.lo, npp, (size_t)c->Np};
     LAUNCH(k_forces<TsumH<true>>, c->nat, 256, 0, c->st, c->nat, R, mc, ts, n, qspin, F, erep_atom);
   } else {
     const MatH& T = final_T_mixed(c);
-    TsumH<false> ts{T.hi, T.lo, nn};
+    TsumH<false> ts{T.hi, T.lo, npp, (size_t)c->Np};
     LAUNCH(k_forces<TsumH<false>>, c->nat, 256, 0, c->st, c->nat, R, mc, ts, n, qspin, F, erep_atom);
   }
 }

@@ -143,11 +143,17 @@ def initial_n(rng: np.random.Generator, n_atoms: int, m0: float = 2.0,
 def make_cell(ncell: int, *, seed: int, sigma: float = 0.05, a: float = 2.87,
               T_K: float = 300.0, params: Optional[ModelParams] = None,
               name: str = "custom", steps: int = 0, m0: float = 2.0,
-              noise: float = 0.1) -> Workload:
-    """Seeded bcc cell with Gaussian displacements (per component, sigma in A)."""
+              noise: float = 0.1, vacancy_frac: float = 0.0) -> Workload:
+    """Seeded bcc cell with Gaussian displacements (per component, sigma in A);
+    vacancy_frac removes that fraction of the sites (rounded down), chosen by
+    the same generator."""
     params = params or ModelParams()
     rng = np.random.Generator(np.random.PCG64(seed))
     R = bcc_positions(ncell, a)
+    n_vac = int(vacancy_frac * R.shape[0])
+    if n_vac > 0:
+        keep = np.sort(rng.permutation(R.shape[0])[n_vac:])
+        R = R[keep]
     R = R + rng.normal(0.0, sigma, size=R.shape)
     V = maxwell_velocities(rng, R.shape[0], params.mass_amu, T_K)
     n0 = initial_n(rng, R.shape[0], m0=m0, noise=noise)
@@ -175,7 +181,30 @@ def fe1024() -> Workload:
                      params=ModelParams(krylov_rank=8), steps=500)
 
 
-WORKLOADS = {"fe16": fe16, "fe128": fe128, "fe1024": fe1024}
+def fe2000() -> Workload:
+    """2000-atom cell (10x10x10 bcc, 18000 orbitals x 2 spins, padded to 18048
+    in the mixed forms), rank 8."""
+    return make_cell(10, seed=SEED_BASE + 5, name="fe2000_bcc10x10x10",
+                     params=ModelParams(krylov_rank=8), steps=10000)
+
+
+def replica_set(count: int = 48) -> list:
+    """Uneven replicas for the batched form: bcc n x n x n cells with n in
+    3..6 (54 to 432 sites), 0-5 % vacancies and displacements sigma in
+    0.03-0.10 A, all drawn from one seeded generator; Krylov rank 6."""
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + 4))
+    out = []
+    for i in range(count):
+        ncell = int(rng.integers(3, 7))
+        vac = float(rng.uniform(0.0, 0.05))
+        sigma = float(rng.uniform(0.03, 0.10))
+        out.append(make_cell(ncell, seed=SEED_BASE + 1000 + i, sigma=sigma, vacancy_frac=vac,
+                             name=f"replica{i:02d}_bcc{ncell}", params=ModelParams(krylov_rank=6),
+                             steps=200))
+    return out
+
+
+WORKLOADS = {"fe16": fe16, "fe128": fe128, "fe1024": fe1024, "fe2000": fe2000}
 
 
 def random_direction(n_atoms: int, seed: int) -> np.ndarray:

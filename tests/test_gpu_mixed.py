@@ -66,6 +66,15 @@ def test_tc_gemm_against_fp64(sxl, prec):
     ctx.close()
 
 
+def _response_bound(ctx, prec):
+    """The response products run on the hi parts alone: each chain step
+    rounds three operands to hi (half an ulp: 2^-12 fp16, 2^-9 bf16), and a
+    relative error entering at step k keeps its size through the later
+    doublings, so the bound is n_r * 3 * 2^-12 (fp16) or 2^-9 (bf16)."""
+    u = 2.0 ** -12 if prec == "fp16" else 2.0 ** -9
+    return ctx.info()["foe_steps"] * 3 * u
+
+
 @pytest.fixture(scope="module")
 def dens128():
     w = wl.fe128()
@@ -88,8 +97,7 @@ def test_mixed_density_and_response(sxl, dens128, prec):
     qv_o, _ = d.response(v)
     rel = np.abs(qv.cpu().numpy() - qv_o).max() / np.abs(qv_o).max()
     print(f"{prec}: response rel err {rel:.2e}")
-    # response products run on the hi parts alone (one product per k step)
-    assert rel < (2e-3 if prec == "fp16" else 2e-2)
+    assert rel < _response_bound(ctx, prec)
     F, en = ctx.forces(w.R, w.n0, energies=True)
     err_f = np.abs(F.cpu().numpy() - energy.forces(d, w.R, w.cell)).max()
     print(f"{prec}: |dF| {err_f:.2e}")
@@ -104,4 +112,40 @@ def test_mixed_density_and_response(sxl, dens128, prec):
     # the 16-bit-pair chain shows up as ~4e-4 eV/atom
     assert per_atom["band"] < (1e-4 if prec == "fp16" else 1e-3)
     assert per_atom["U"] < (1e-3 if prec == "fp16" else 5e-3)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("ncell,vac", [(3, 0.0), (2, 0.0), (3, 0.04)])
+def test_mixed_padded_chain(sxl, prec, ncell, vac):
+    """Cells whose 9 N_at is not a multiple of 64 (54 atoms: N = 486 -> 512;
+    16 atoms: 144 -> 192; 52 atoms with vacancies: 468 -> 512) run the
+    chain on the padded dimension; q, m, the response, the forces and the
+    shadow energy match the FP64 oracle with the 128-atom tolerances."""
+    w = wl.make_cell(ncell, seed=5400 + ncell, sigma=0.06, vacancy_frac=vac, name="padded")
+    nat = w.R.shape[0]
+    assert (9 * nat) % 64 != 0
+    d = electronic.density(w.R, w.cell, w.n0, w.params)
+    ctx = sxl.Context(w.params, nat, w.cell, prec)
+    q, mu = ctx.density(w.R, w.n0)
+    q = q.cpu().numpy()
+    err_q = np.abs(q - d.q).max()
+    err_m = np.abs((q[:nat] - q[nat:]) - d.spin).max()
+    tol = 1e-4 if prec == "fp16" else 2e-3
+    print(f"padded {nat} {prec}: |dq| {err_q:.2e} |dm| {err_m:.2e} |dmu| {abs(mu - d.mu):.2e}")
+    assert err_q < tol and err_m < tol
+    v = wl.random_direction(nat, 12)
+    qv, _ = ctx.response(v)
+    qv_o, _ = d.response(v)
+    rel = np.abs(qv.cpu().numpy() - qv_o).max() / np.abs(qv_o).max()
+    assert rel < _response_bound(ctx, prec), rel
+    F, en = ctx.forces(w.R, w.n0, energies=True)
+    err_f = np.abs(F.cpu().numpy() - energy.forces(d, w.R, w.cell)).max()
+    assert err_f < (1e-3 if prec == "fp16" else 2e-2), err_f
+    from oracle import model
+    e_o = energy.shadow_energy(d, model.build_h0(w.R, w.cell, w.params),
+                               model.repulsive_energy(w.R, w.cell, w.params))
+    dU = abs(en["U"] - e_o["U"]) / nat
+    print(f"padded {nat} {prec}: rel {rel:.2e} |dF| {err_f:.2e} dU/atom {dU:.2e}")
+    assert dU < (1e-3 if prec == "fp16" else 5e-3)
     ctx.close()
