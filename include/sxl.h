@@ -82,8 +82,9 @@ typedef struct {
   int    foe_steps;          /* recursion depth; 0 = choose from spectral bounds */
   double foe_u_max;          /* bound on |eig(U)| that fixes the depth when
                                 foe_steps == 0: 0 = 0.05 over the whole
-                                search window for SXL_FP64, 0.5 about each
-                                pass's mu for the mixed forms               */
+                                search window for SXL_FP64, 1 about each
+                                pass's mu for the mixed forms (which refuse
+                                a start beyond |U| = 1)                      */
   int    mu_max_iter;        /* cap on chemical-potential Newton passes (0 = 30) */
   double mu_tol;             /* |sum Tr D - N_e| tolerance (0 = 1e-10 for
                                 SXL_FP64, 1e-6 N_e for the mixed forms)      */

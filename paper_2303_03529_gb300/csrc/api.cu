@@ -219,11 +219,11 @@ static int density(sxl_ctx* c, const double* R, const double* n, double mu_guess
   // Depth of the expansion: |U| = |y| / 2^nr <= u_t for every state.
   // fp64 form: u_t = 0.05 over the whole search window (one depth for all
   // passes), so the fifth-order start is exact to ~1e-11 in the effective
-  // argument of every state.  Mixed forms: u_t = 0.5 about the pass's own mu.
+  // argument of every state.  Mixed forms: u_t = 1 about the pass's own mu.
   // The start then distorts the argument of states far from mu (which stay
   // saturated) but not of those near mu (|u| tiny), so q, F and the response
   // do not see it; the entropy takes the known distortion into account.
-  const double ut = c->p.foe_u_max > 0 ? c->p.foe_u_max : (mixed ? 0.5 : 0.05);
+  const double ut = c->p.foe_u_max > 0 ? c->p.foe_u_max : (mixed ? 1.0 : 0.05);
   const double window = hi - lo;  // lo and hi narrow as the search brackets mu
   auto set_depth = [&](double m) {
     if (c->p.foe_steps > 0) {

@@ -663,21 +663,32 @@ void energy_terms(sxl_ctx* c, const double* n, const double* erep_atom, double* 
 // on |eig(U)|, and its polynomial start stays accurate well beyond it.
 #define LZ 32
 // w[s] = H_s v[s] - beta_prev v_prev[s]; partial alpha = v . w  (warp per row)
+// w_s = H_s v_s - beta_s vprev_s for both spins (H_s = H0 + diagonal
+// shift), one warp per row of H0, which is read once for the two spins
 __global__ void k_lz_matvec(int nat, const double* __restrict__ H0, const double* __restrict__ shift,
                             const double* __restrict__ v, const double* __restrict__ vprev,
                             const double* __restrict__ beta, double* w) {
   const int N = nat * NORB;
-  int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   int lane = threadIdx.x & 31;
-  if (row >= 2 * N) return;
-  int s = row / N, i = row % N;
-  const double* vs = v + (size_t)s * N;
-  double acc = 0.0;
-  for (int j = lane; j < N; j += 32) acc += H0[(size_t)i * N + j] * vs[j];
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (i >= N) return;
+  const double* v0 = v;
+  const double* v1 = v + N;
+  double a0 = 0.0, a1 = 0.0;
+  for (int j = lane; j < N; j += 32) {
+    const double h = H0[(size_t)i * N + j];
+    a0 += h * v0[j];
+    a1 += h * v1[j];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a0 += __shfl_down_sync(0xffffffffu, a0, o);
+    a1 += __shfl_down_sync(0xffffffffu, a1, o);
+  }
   if (lane == 0) {
-    acc += shift[s * nat + i / NORB] * vs[i];
-    w[row] = acc - beta[s] * vprev[row];
+    a0 += shift[i / NORB] * v0[i];
+    a1 += shift[nat + i / NORB] * v1[i];
+    w[i] = a0 - beta[0] * vprev[i];
+    w[N + i] = a1 - beta[1] * vprev[N + i];
   }
 }
 
@@ -764,35 +775,45 @@ __device__ int sturm_count(const double* a, const double* b, int m, double x) {
   return cnt;
 }
 
+// Extreme eigenvalues of the two Lanczos tridiagonals by multisection of the
+// Sturm count: warp 2 s + e (spin s; e = 0 smallest, 1 largest) splits its
+// bracket into 33 parts per round, one Sturm count per lane, 14 rounds
+// (33^14 > 2^64: the resolution of 64 bisection steps).  Lane 0 of thread
+// block writes [min over spins - margin, max + margin], margin = max(2 b_m, 1).
 __global__ void k_lz_bounds(const double* alphas, const double* betas, double* out) {
-  if (threadIdx.x != 0) return;
-  double lo_all = 1e300, hi_all = -1e300;
-  for (int s = 0; s < 2; ++s) {
-    const double* a = alphas + s * LZ;
-    const double* b = betas + s * LZ;
-    int m = LZ;
-    for (int i = 0; i < LZ; ++i)
-      if (!(b[i] > 1e-12)) { m = i + 1; break; }
-    double r = 0.0;
-    for (int i = 0; i < m; ++i) r = fmax(r, fabs(a[i]) + (i > 0 ? b[i - 1] : 0.0) + b[i]);
-    double lo = -r, hi = r;
-    for (int k = 0; k < 64; ++k) {  // smallest eigenvalue (2^-64 of the Gershgorin width)
-      double mid = 0.5 * (lo + hi);
-      if (sturm_count(a, b, m, mid) >= 1) hi = mid; else lo = mid;
-    }
-    double emin = hi;
-    lo = -r; hi = r;
-    for (int k = 0; k < 64; ++k) {  // largest eigenvalue
-      double mid = 0.5 * (lo + hi);
-      if (sturm_count(a, b, m, mid) >= m) hi = mid; else lo = mid;
-    }
-    double emax = lo;
-    double margin = fmax(2.0 * b[m - 1], 1.0);
-    lo_all = fmin(lo_all, emin - margin);
-    hi_all = fmax(hi_all, emax + margin);
+  __shared__ double res[4];
+  __shared__ double marg[2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = warp >> 1, e = warp & 1;
+  const double* a = alphas + s * LZ;
+  const double* b = betas + s * LZ;
+  int m = LZ;
+  for (int i = 0; i < LZ; ++i)
+    if (!(b[i] > 1e-12)) { m = i + 1; break; }
+  double r = 0.0;
+  for (int i = 0; i < m; ++i) r = fmax(r, fabs(a[i]) + (i > 0 ? b[i - 1] : 0.0) + b[i]);
+  // smallest eigenvalue: the least x with count(x) >= 1; largest: the least
+  // x with count(x) >= m (its bracket's lower end is the estimate)
+  const int need = e == 0 ? 1 : m;
+  double lo = -r, hi = r;
+  for (int round = 0; round < 14; ++round) {
+    const double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+    const unsigned mask = __ballot_sync(0xffffffffu, sturm_count(a, b, m, x) >= need);
+    const int k = mask ? __ffs(mask) - 1 : 32;
+    const double nlo = k == 0 ? lo : lo + (hi - lo) * (double)k / 33.0;
+    const double nhi = k == 32 ? hi : lo + (hi - lo) * (double)(k + 1) / 33.0;
+    lo = nlo;
+    hi = nhi;
   }
-  out[0] = lo_all;
-  out[1] = hi_all;
+  if (lane == 0) {
+    res[warp] = e == 0 ? hi : lo;
+    if (e == 0) marg[s] = fmax(2.0 * b[m - 1], 1.0);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    out[0] = fmin(res[0] - marg[0], res[2] - marg[1]);
+    out[1] = fmax(res[1] + marg[0], res[3] + marg[1]);
+  }
 }
 
 void lanczos_bounds(sxl_ctx* c, double* out2) {
@@ -807,9 +828,9 @@ void lanczos_bounds(sxl_ctx* c, double* out2) {
   LAUNCH(k_lz_normalize, 2, 1024, 0, c->st, N, v);
   int wpb = 8;
   for (int it = 0; it < LZ; ++it) {
-    LAUNCH(k_lz_matvec, (2 * N + wpb - 1) / wpb, 32 * wpb, 0, c->st, c->nat, c->H0, c->shift, v,
+    LAUNCH(k_lz_matvec, (N + wpb - 1) / wpb, 32 * wpb, 0, c->st, c->nat, c->H0, c->shift, v,
            vprev, beta, w);
     LAUNCH(k_lz_update, 2, 1024, 0, c->st, N, it, v, vprev, w, beta, al, be);
   }
-  LAUNCH(k_lz_bounds, 1, 32, 0, c->st, al, be, out2);
+  LAUNCH(k_lz_bounds, 1, 128, 0, c->st, al, be, out2);
 }

@@ -919,9 +919,10 @@ int foe_mixed(sxl_ctx* c, double mu, double* stats_dev) {
   SXL_TRY(ensure_chain_h(c, nr));
   const bool split = true;
   c->umax = c->scale * std::max(std::fabs(c->lam_max - mu), std::fabs(mu - c->lam_min));
-  // the start polynomial is monotone with |p(u)| < 1 up to |u| ~ 1.2
-  if (!(c->umax <= 1.2))
-    return sxl_fail(c, SXL_E_ARG, "expansion start out of range (|U| > 1.2): raise foe_steps");
+  // the start polynomial is monotone with |p(u)| < 1 up to |u| ~ 1.2; the
+  // entropy's start correction is fitted on |u| <= 1
+  if (!(c->umax <= 1.0 + 1e-9))
+    return sxl_fail(c, SXL_E_ARG, "expansion start out of range (|U| > 1): raise foe_steps");
   // padding orbitals (Np > N) sit at the upper spectral bound: |u| <= umax,
   // and with mu inside the spectrum they stay empty (f ~ exp(-beta (lam_max - mu)))
   size_t total = (size_t)Np * Np;
@@ -1325,13 +1326,13 @@ __global__ void k_dot_hl_partial(long long len, const uint16_t* ah, const uint16
 // Tr(Y' T') = 2^nr <U, T'> - sh Tr T'.
 __global__ void k_entropy_combine(int N, int nr, const double* ld, const double* dots, double* out,
                                   double sh, const double* ldsh, const double* trT,
-                                  const double* corr, double a3) {
+                                  const double* corr, double wcorr) {
   if (threadIdx.x != 0) return;
   double tot = 0.0;
   const double lch = sh != 0.0 ? log(cosh(sh)) : 0.0;
   for (int s = 0; s < 2; ++s) {
     double v = -N * 0.69314718055994531 + ldexp(1.0, nr - 1) * ld[s] +
-               ldexp(1.0, nr) * (dots[s] + a3 * corr[s]);
+               ldexp(1.0, nr) * (dots[s] + wcorr * corr[s]);
     for (int k = 0; k < nr; ++k) v += ldexp(1.0, nr - 1 - k) * ld[2 * (k + 1) + s];
     v -= N * lch + ldsh[s];
     v -= sh * trT[s];
@@ -1404,31 +1405,35 @@ int entropy_mixed(sxl_ctx* c, double* out_dev) {
   }
   // The fifth-order start is tanh of artanh(p(U)) = U + delta(U), not of U:
   // the chain's argument is 2^nr (U + delta(U)), and Tr(Y T) takes the term
-  // 2^nr <delta(U), T> with delta(u) = u^7 (17/315 + 13 u^2/405 + 37 u^4/7425
-  // + 2 u^6/5265) (relative error < 3e-4 for |u| <= 0.5).  In S' = U^2 / a,
-  // a = u_max^2 (spectrum in [0, 1]): delta(U) = a^3 U S'^3 g(S').
+  // 2^nr <delta(U), T>.  delta(u) = u^7 g(u^2) with g of degree 6 fitted on
+  // |u| <= 1 (csrc/fit_start_distortion.py; max absolute error 1.3e-7), in
+  // split products on S = U^2 by Horner's rule.
+  static const double gc[7] = {0.054831031685028641, 0.021564109913214173, 0.056144308567421674,
+                               -0.12768677643954198, 0.17928192499418042, -0.12596950090979318,
+                               0.040447056725233073};
   double* corr = c->red + 3176;  // 2
   CUDA_TRY(c, cudaMemsetAsync(corr, 0, 2 * sizeof(double), c->st));
-  double a3 = 0.0;
+  double wcorr = 0.0;
   if (c->umax > 0.02) {
-    const double a = c->umax * c->umax;
-    a3 = a * a * a;
-    const double d7 = 17.0 / 315.0, d9 = 13.0 / 405.0 * a, d11 = 37.0 / 7425.0 * a * a,
-                 d13 = 2.0 / 5265.0 * a * a * a;
-    axpy_diag_h(c, c->hX0, 1.0 / a, c->hS, 0.0);                                    // S'
-    SXL_TRY(gemm_tc(c, c->hX0, c->hX0, c->hX1, 1.f, nullptr, 0.f, 0.f, true, false));  // S'^2
-    axpy_diag_h(c, c->hP, d13, c->hX0, d11);
-    SXL_TRY(gemm_tc(c, c->hX1, c->hP, c->hG1, 1.f, &c->hX0, (float)d9, (float)d7, true, false));
-    SXL_TRY(gemm_tc(c, c->hX1, c->hX0, c->hP, 1.f, nullptr, 0.f, 0.f, true, false));   // S'^3
-    SXL_TRY(gemm_tc(c, c->hP, c->hG1, c->hX1, 1.f, nullptr, 0.f, 0.f, true, false));   // S'^3 g
-    SXL_TRY(gemm_tc(c, c->hU, c->hX1, c->hP, 1.f, nullptr, 0.f, 0.f, true, false));    // U S'^3 g
+    wcorr = 1.0;
+    axpy_diag_h(c, c->hX0, gc[6], c->hS, gc[5]);
+    const MatH* cur = &c->hX0;
+    for (int j = 4; j >= 0; --j) {
+      const MatH* nxt = (cur == &c->hX0) ? &c->hX1 : &c->hX0;
+      SXL_TRY(gemm_tc(c, c->hS, *cur, *nxt, 1.f, nullptr, 0.f, (float)gc[j], true, true));
+      cur = nxt;
+    }                                                                                   // g(S)
+    SXL_TRY(gemm_tc(c, c->hS, c->hS, c->hP, 1.f, nullptr, 0.f, 0.f, true, true));      // S^2
+    SXL_TRY(gemm_tc(c, c->hP, c->hS, c->hG1, 1.f, nullptr, 0.f, 0.f, true, true));     // S^3
+    SXL_TRY(gemm_tc(c, c->hG1, *cur, c->hP, 1.f, nullptr, 0.f, 0.f, true, true));      // S^3 g
+    SXL_TRY(gemm_tc(c, c->hU, c->hP, c->hG1, 1.f, nullptr, 0.f, 0.f, true, true));     // delta(U)
     for (int s = 0; s < 2; ++s) {
-      DISPATCH(c, k_dot_hl_partial, 128, 256, 0, (long long)nn, c->hP.hi + s * nn,
-               c->hP.lo + s * nn, Tf.hi + s * nn, Tf.lo + s * nn, c->red + 2048);
+      DISPATCH(c, k_dot_hl_partial, 128, 256, 0, (long long)nn, c->hG1.hi + s * nn,
+               c->hG1.lo + s * nn, Tf.hi + s * nn, Tf.lo + s * nn, c->red + 2048);
       LAUNCH(k_sum_parts, 1, 256, 0, c->st, 128, c->red + 2048, corr + s);
     }
   }
   const double sh = c->teff_valid ? std::atanh(c->shift_tau) : 0.0;
-  LAUNCH(k_entropy_combine, 1, 32, 0, c->st, N, nr, ld, dots, out_dev, sh, ldsh, trT, corr, a3);
+  LAUNCH(k_entropy_combine, 1, 32, 0, c->st, N, nr, ld, dots, out_dev, sh, ldsh, trT, corr, wcorr);
   return SXL_OK;
 }

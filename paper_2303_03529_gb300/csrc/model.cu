@@ -3,49 +3,48 @@
 // Eqs. ELatte, ShadowELatte, EqMot).
 //
 // The two-center element E_ab(d) of orbitals a at the origin and b at d is
-// evaluated by sk_elem<T>.  T = double gives the value (Hamiltonian build);
-// T = Dual3 carries the gradient with respect to the three components of d
-// (forces), so no derivative formula is written by hand.
+// evaluated by sk_upper<T> (a <= b; the rest by parity).  T = double gives
+// the value (Hamiltonian build); T = Dual1 carries the derivative with
+// respect to one component of d (forces, one pass per direction), so no
+// derivative formula is written by hand.
 #include "common.cuh"
 
 // ---------------------------------------------------------------------------
-// forward-mode dual number with a 3-component gradient
-struct Dual3 {
-  double v, g0, g1, g2;
-  __device__ Dual3() {}
-  __device__ Dual3(double x) : v(x), g0(0), g1(0), g2(0) {}
-  __device__ Dual3(double x, double a, double b, double c) : v(x), g0(a), g1(b), g2(c) {}
+// forward-mode dual number with one gradient component (the forces run each
+// bond once per Cartesian direction, which keeps the kernel free of spills)
+struct Dual1 {
+  double v, g;
+  __device__ Dual1() {}
+  __device__ Dual1(double x) : v(x), g(0) {}
+  __device__ Dual1(double x, double d) : v(x), g(d) {}
 };
-__device__ inline Dual3 operator+(Dual3 a, Dual3 b) { return Dual3(a.v + b.v, a.g0 + b.g0, a.g1 + b.g1, a.g2 + b.g2); }
-__device__ inline Dual3 operator-(Dual3 a, Dual3 b) { return Dual3(a.v - b.v, a.g0 - b.g0, a.g1 - b.g1, a.g2 - b.g2); }
-__device__ inline Dual3 operator-(Dual3 a) { return Dual3(-a.v, -a.g0, -a.g1, -a.g2); }
-__device__ inline Dual3 operator*(Dual3 a, Dual3 b) {
-  return Dual3(a.v * b.v, a.g0 * b.v + a.v * b.g0, a.g1 * b.v + a.v * b.g1, a.g2 * b.v + a.v * b.g2);
-}
-__device__ inline Dual3 operator*(double s, Dual3 a) { return Dual3(s * a.v, s * a.g0, s * a.g1, s * a.g2); }
-__device__ inline Dual3 operator*(Dual3 a, double s) { return s * a; }
-__device__ inline Dual3 operator+(double s, Dual3 a) { return Dual3(s + a.v, a.g0, a.g1, a.g2); }
-__device__ inline Dual3 operator+(Dual3 a, double s) { return s + a; }
-__device__ inline Dual3 operator-(double s, Dual3 a) { return Dual3(s - a.v, -a.g0, -a.g1, -a.g2); }
-__device__ inline Dual3 operator-(Dual3 a, double s) { return Dual3(a.v - s, a.g0, a.g1, a.g2); }
-__device__ inline Dual3 operator/(Dual3 a, Dual3 b) {
+__device__ inline Dual1 operator+(Dual1 a, Dual1 b) { return Dual1(a.v + b.v, a.g + b.g); }
+__device__ inline Dual1 operator-(Dual1 a, Dual1 b) { return Dual1(a.v - b.v, a.g - b.g); }
+__device__ inline Dual1 operator-(Dual1 a) { return Dual1(-a.v, -a.g); }
+__device__ inline Dual1 operator*(Dual1 a, Dual1 b) { return Dual1(a.v * b.v, a.g * b.v + a.v * b.g); }
+__device__ inline Dual1 operator*(double s, Dual1 a) { return Dual1(s * a.v, s * a.g); }
+__device__ inline Dual1 operator*(Dual1 a, double s) { return s * a; }
+__device__ inline Dual1 operator+(double s, Dual1 a) { return Dual1(s + a.v, a.g); }
+__device__ inline Dual1 operator+(Dual1 a, double s) { return s + a; }
+__device__ inline Dual1 operator-(double s, Dual1 a) { return Dual1(s - a.v, -a.g); }
+__device__ inline Dual1 operator-(Dual1 a, double s) { return Dual1(a.v - s, a.g); }
+__device__ inline Dual1 operator/(Dual1 a, Dual1 b) {
   double iv = 1.0 / b.v;
   double q = a.v * iv;
-  return Dual3(q, (a.g0 - q * b.g0) * iv, (a.g1 - q * b.g1) * iv, (a.g2 - q * b.g2) * iv);
+  return Dual1(q, (a.g - q * b.g) * iv);
 }
-__device__ inline Dual3 dsqrt(Dual3 a) {
+__device__ inline Dual1 dsqrt(Dual1 a) {
   double s = sqrt(a.v);
-  double h = 0.5 / s;
-  return Dual3(s, a.g0 * h, a.g1 * h, a.g2 * h);
+  return Dual1(s, a.g * (0.5 / s));
 }
-__device__ inline Dual3 dexp(Dual3 a) {
+__device__ inline Dual1 dexp(Dual1 a) {
   double e = exp(a.v);
-  return Dual3(e, a.g0 * e, a.g1 * e, a.g2 * e);
+  return Dual1(e, a.g * e);
 }
+__device__ inline double val(const Dual1& a) { return a.v; }
 __device__ inline double dsqrt(double a) { return sqrt(a); }
 __device__ inline double dexp(double a) { return exp(a); }
 __device__ inline double val(double a) { return a; }
-__device__ inline double val(const Dual3& a) { return a.v; }
 
 ModelConst model_const(const sxl_params& p) {
   ModelConst m;
@@ -72,19 +71,21 @@ __device__ inline T switch_fn(T r, const ModelConst& m) {
 }
 
 // Slater-Koster two-center element for a <= b (orbital order s, px, py, pz,
-// dxy, dyz, dzx, dx2-y2, d3z2-r2); V = the ten bond integrals at |d|.
+// dxy, dyz, dzx, dx2-y2, d3z2-r2); V = the ten bond integrals.  The element
+// is linear in V: callers pass the prefactors V0 and multiply by the radial
+// factor, so only the direction cosines carry the dual-number gradient.
 // key = b for a = 0, else 10 a + (b - a): s-*: 0..8, x-*: 10..17, y-*: 20..26,
 // z-*: 30..35, xy-*: 40..44, yz-*: 50..53, zx-*: 60..62, x2-*: 70..71, z2: 80.
 template <class T>
-__device__ T sk_upper(int key, const T& l, const T& m, const T& n, const T* V) {
+__device__ T sk_upper(int key, const T& l, const T& m, const T& n, const double* V) {
   const double s3 = 1.7320508075688772;
-  const T &sss = V[0], &sps = V[1], &sds = V[2], &pps = V[3], &ppp = V[4];
-  const T &pds = V[5], &pdp = V[6], &dds = V[7], &ddp = V[8], &ddd = V[9];
+  const double sss = V[0], sps = V[1], sds = V[2], pps = V[3], ppp = V[4];
+  const double pds = V[5], pdp = V[6], dds = V[7], ddp = V[8], ddd = V[9];
   T l2 = l * l, m2 = m * m, n2 = n * n;
   T lm2 = l2 - m2;
   T z2f = n2 - 0.5 * (l2 + m2);
   switch (key) {
-    case 0:  return sss;                                     // s s
+    case 0:  return T(sss);                                  // s s
     case 1:  return l * sps;                                 // s x
     case 2:  return m * sps;                                 // s y
     case 3:  return n * sps;                                 // s z
@@ -133,43 +134,38 @@ __device__ T sk_upper(int key, const T& l, const T& m, const T& n, const T* V) {
   }
 }
 
-// general (a, b): lower entries by E_ba(d) = (-1)^(l_a + l_b) E_ab(d)
-template <class T>
-__device__ inline T sk_elem(int a, int b, const T& l, const T& m, const T& n, const T* V) {
-  if (a <= b) return sk_upper<T>(a == 0 ? b : 10 * a + (b - a), l, m, n, V);
-  T v = sk_elem<T>(b, a, l, m, n, V);
-  return ((c_ell[a] + c_ell[b]) & 1) ? -v : v;
-}
-
-// Bond integrals at distance r and the direction cosines of d.
+// Direction cosines of d, its length and the radial factor of the bond
+// integrals (V_x = V0_x rad); lower elements follow from the upper ones by
+// E_ba(d) = (-1)^(l_a + l_b) E_ab(d).
 template <class T>
 __device__ inline void bond_setup(const T& dx, const T& dy, const T& dz, const ModelConst& mc,
-                                  T& l, T& m, T& n, T* V, T& r) {
+                                  T& l, T& m, T& n, T& rad, T& r) {
   r = dsqrt(dx * dx + dy * dy + dz * dz);
   T ir = T(1.0) / r;
   l = dx * ir; m = dy * ir; n = dz * ir;
-  T rad = dexp(-mc.q_decay * (r - mc.r0)) * switch_fn<T>(r, mc);
-#pragma unroll
-  for (int b = 0; b < 10; ++b) V[b] = mc.V0[b] * rad;
+  rad = dexp(-mc.q_decay * (r - mc.r0)) * switch_fn<T>(r, mc);
 }
 
 __device__ inline double min_image(double d, double L) { return d - L * rint(d / L); }
 
 // ---------------------------------------------------------------------------
-// H0: block (K) writes the 9 rows of atom K; each thread owns columns j.
-// For each column (atom J, orbital b) it sums E_ab over the 27 image shifts
-// of the minimum-image displacement with 0 < r < r_cut (fixed order, so the
-// sum is deterministic), for a = 0..8.
+// H0: block (K) writes the 9 rows of atom K; each thread owns partner atoms
+// J (strided) and writes their 9 x 9 block: the on-site energies for J = K,
+// then E_ab summed over the 27 image shifts of the minimum-image displacement
+// with 0 < r < r_cut (fixed order: deterministic).  The 45 elements a <= b
+// are unrolled (the key of every lane is the same, so the Slater-Koster
+// cases do not diverge) and the lower ones follow by parity.
 __global__ void k_build_h0(int nat, const double* __restrict__ R, ModelConst mc,
                            double* __restrict__ H0) {
   const int K = blockIdx.x;
   const int N = nat * NORB;
   const double Kx = R[3 * K], Ky = R[3 * K + 1], Kz = R[3 * K + 2];
-  for (int j = threadIdx.x; j < N; j += blockDim.x) {
-    const int J = j / NORB, b = j % NORB;
-    double acc[NORB];
+  for (int J = threadIdx.x; J < nat; J += blockDim.x) {
+    double* blk = H0 + (size_t)(NORB * K) * N + NORB * J;  // row stride N
 #pragma unroll
-    for (int a = 0; a < NORB; ++a) acc[a] = 0.0;
+    for (int a = 0; a < NORB; ++a)
+#pragma unroll
+      for (int b = 0; b < NORB; ++b) blk[(size_t)a * N + b] = (J == K && a == b) ? mc.eps[c_ell[a]] : 0.0;
     double dx0 = min_image(R[3 * J] - Kx, mc.cell[0]);
     double dy0 = min_image(R[3 * J + 1] - Ky, mc.cell[1]);
     double dz0 = min_image(R[3 * J + 2] - Kz, mc.cell[2]);
@@ -179,14 +175,17 @@ __global__ void k_build_h0(int nat, const double* __restrict__ R, ModelConst mc,
       double dz = dz0 + (s % 3 - 1) * mc.cell[2];
       double r2 = dx * dx + dy * dy + dz * dz;
       if (r2 >= mc.r_cut * mc.r_cut || r2 < 1e-16) continue;
-      double l, m, n, r, V[10];
-      bond_setup<double>(dx, dy, dz, mc, l, m, n, V, r);
+      double l, m, n, r, rad;
+      bond_setup<double>(dx, dy, dz, mc, l, m, n, rad, r);
 #pragma unroll
-      for (int a = 0; a < NORB; ++a) acc[a] += sk_elem<double>(a, b, l, m, n, V);
+      for (int a = 0; a < NORB; ++a)
+#pragma unroll
+        for (int b = a; b < NORB; ++b) {
+          const double e = rad * sk_upper<double>(a == 0 ? b : 10 * a + (b - a), l, m, n, mc.V0);
+          blk[(size_t)a * N + b] += e;
+          if (b != a) blk[(size_t)b * N + a] += ((c_ell[a] + c_ell[b]) & 1) ? -e : e;
+        }
     }
-    if (J == K) acc[b] += mc.eps[c_ell[b]];
-#pragma unroll
-    for (int a = 0; a < NORB; ++a) H0[(size_t)(NORB * K + a) * N + j] = acc[a];
   }
 }
 
@@ -252,7 +251,7 @@ void launch_spin_shift(sxl_ctx* c, const double* n, double* out) {
 }
 
 // ---------------------------------------------------------------------------
-// Forces at constant n.  Block per atom K, warps over partner atoms J:
+// Forces at constant n.  Block per atom K, threads over partner atoms J:
 //   band:  F_K += 2 sum_{J != K, images} sum_ab Dsum_{Ka,Jb} dE_ab/dd
 //          with Dsum = D_up + D_dn = -(T_up + T_dn)/2 off the diagonal blocks,
 //   repulsion: F_K += sum_images dPhi(|d|)/dd, E_rep,K = 1/2 sum Phi,
@@ -300,43 +299,48 @@ __global__ void __launch_bounds__(256) k_forces(int nat, const double* __restric
                                                 double* __restrict__ F,
                                                 double* __restrict__ erep) {
   const int K = blockIdx.x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nwarps = blockDim.x >> 5;
   double fx = 0.0, fy = 0.0, fz = 0.0, er = 0.0;
   const double Kx = R[3 * K], Ky = R[3 * K + 1], Kz = R[3 * K + 2];
-  for (int J = warp; J < nat; J += nwarps) {
+  // threads own partner atoms J (strided); per in-range image, the loop over
+  // the 45 elements a <= b runs in step on every lane (one Slater-Koster case
+  // at a time, no divergence) and each element also serves its parity
+  // partner (b, a)
+  for (int J = threadIdx.x; J < nat; J += blockDim.x) {
     if (J == K) continue;  // self-image bonds do not depend on R_K
     double dx0 = min_image(R[3 * J] - Kx, mc.cell[0]);
     double dy0 = min_image(R[3 * J + 1] - Ky, mc.cell[1]);
     double dz0 = min_image(R[3 * J + 2] - Kz, mc.cell[2]);
-    bool in = false;
-    if (lane < 27) {
-      double dx = dx0 + (lane / 9 - 1) * mc.cell[0];
-      double dy = dy0 + ((lane / 3) % 3 - 1) * mc.cell[1];
-      double dz = dz0 + (lane % 3 - 1) * mc.cell[2];
-      in = dx * dx + dy * dy + dz * dz < mc.r_cut * mc.r_cut;
-    }
-    unsigned mask = __ballot_sync(0xffffffffu, in);
-    while (mask) {
-      int s = __ffs(mask) - 1;
-      mask &= mask - 1;
-      Dual3 dx(dx0 + (s / 9 - 1) * mc.cell[0], 1.0, 0.0, 0.0);
-      Dual3 dy(dy0 + ((s / 3) % 3 - 1) * mc.cell[1], 0.0, 1.0, 0.0);
-      Dual3 dz(dz0 + (s % 3 - 1) * mc.cell[2], 0.0, 0.0, 1.0);
-      Dual3 l, m, nn, V[10], r;
-      bond_setup<Dual3>(dx, dy, dz, mc, l, m, nn, V, r);
-      for (int e = lane; e < NORB * NORB; e += 32) {
-        int a = e / NORB, b = e % NORB;
-        Dual3 E = sk_elem<Dual3>(a, b, l, m, nn, V);
-        double dsum = -0.5 * tsum_at<TS>(ts, (size_t)(NORB * K + a), (size_t)(NORB * J + b));
-        fx += 2.0 * dsum * E.g0;
-        fy += 2.0 * dsum * E.g1;
-        fz += 2.0 * dsum * E.g2;
-      }
-      if (lane == 0 && mc.rep_A != 0.0) {
-        Dual3 phi = mc.rep_A * dexp(-mc.rep_b * (r - mc.r0)) * switch_fn<Dual3>(r, mc);
-        fx += phi.g0; fy += phi.g1; fz += phi.g2;
-        er += 0.5 * phi.v;
+    for (int s = 0; s < 27; ++s) {
+      const double ex = dx0 + (s / 9 - 1) * mc.cell[0];
+      const double ey = dy0 + ((s / 3) % 3 - 1) * mc.cell[1];
+      const double ez = dz0 + (s % 3 - 1) * mc.cell[2];
+      if (ex * ex + ey * ey + ez * ez >= mc.r_cut * mc.r_cut) continue;
+#pragma unroll 1
+      for (int dir = 0; dir < 3; ++dir) {
+        Dual1 dx(ex, dir == 0 ? 1.0 : 0.0), dy(ey, dir == 1 ? 1.0 : 0.0), dz(ez, dir == 2 ? 1.0 : 0.0);
+        Dual1 l, m, nn, rad, r;
+        bond_setup<Dual1>(dx, dy, dz, mc, l, m, nn, rad, r);
+        double g = 0.0;
+#pragma unroll 1
+        for (int a = 0; a < NORB; ++a)
+#pragma unroll 1
+          for (int b = a; b < NORB; ++b) {
+            const Dual1 E = rad * sk_upper<Dual1>(a == 0 ? b : 10 * a + (b - a), l, m, nn, mc.V0);
+            double w = -0.5 * tsum_at<TS>(ts, (size_t)(NORB * K + a), (size_t)(NORB * J + b));
+            if (b != a) {
+              const double wb = -0.5 * tsum_at<TS>(ts, (size_t)(NORB * K + b), (size_t)(NORB * J + a));
+              w += ((c_ell[a] + c_ell[b]) & 1) ? -wb : wb;
+            }
+            g += 2.0 * w * E.g;
+          }
+        if (mc.rep_A != 0.0) {
+          Dual1 phi = mc.rep_A * dexp(-mc.rep_b * (r - mc.r0)) * switch_fn<Dual1>(r, mc);
+          g += phi.g;
+          if (dir == 0) er += 0.5 * phi.v;
+        }
+        if (dir == 0) fx += g;
+        else if (dir == 1) fy += g;
+        else fz += g;
       }
     }
   }
