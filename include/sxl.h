@@ -187,6 +187,42 @@ int xlbomd_step(sxl_ctx* ctx, int nsteps, double* stats_host);
 int scf_solve(sxl_ctx* ctx, const double* R_dev, double* n_dev, double tol,
               int max_iter, int* iters_out, double* rms_out);
 
+/* SCF mixers for the comparison of Sec. IV (Fig. SCF). */
+enum { SXL_MIX_KERNEL = 0, SXL_MIX_LINEAR = 1, SXL_MIX_DIIS = 2 };
+typedef struct {
+  int    mixer;          /* SXL_MIX_KERNEL, SXL_MIX_LINEAR or SXL_MIX_DIIS     */
+  double lin_mix;        /* linear mixing coefficient (0 = 0.06)              */
+  double switch_rms;     /* RMS(q - n) below which the kernel or DIIS mixer
+                            takes over from linear mixing (0 = 0.05)          */
+  int    diis_hist;      /* DIIS history length (0 = 8; at most 16)           */
+  double diis_mix;       /* DIIS step: n = sum c_i (n_i + diis_mix f_i) (0 = 0.1) */
+  double krylov_rel_tol; /* kernel mixer: adaptive-rank stop (0 = 0.1)        */
+} sxl_scf_opts;
+
+/* scf_solve with a choice of mixer (opts may be NULL: the kernel mixer with
+ * the defaults above).  DIIS keeps the last diis_hist pairs (n_i, f_i =
+ * q[n_i] - n_i) and takes the c minimizing |sum c_i f_i| with sum c_i = 1
+ * (bordered system, Gaussian elimination with partial pivoting on the
+ * device; a singular system falls back to the newest input).  rms_hist_host
+ * (may be NULL, max_iter doubles) receives RMS(q - n) of every iteration.
+ * Same returns as scf_solve; SXL_E_ARG for an unknown mixer. */
+int scf_solve_ex(sxl_ctx* ctx, const double* R_dev, double* n_dev, double tol, int max_iter,
+                 const sxl_scf_opts* opts, double* rms_hist_host, int* iters_out,
+                 double* rms_out);
+
+/* Regular Born-Oppenheimer MD (the paper's comparison, Sec. IV): nsteps
+ * velocity-Verlet steps from the context state, each with the forces of the
+ * SCF ground state at the new positions.  The SCF starts from the previous
+ * step's converged n (the newest n of the state) and runs with opts to
+ * RMS(q - n) < tol (at most max_iter iterations, else
+ * SXL_E_NO_CONVERGENCE).  The first call converges the SCF at the initial
+ * positions first.  stats_host as for xlbomd_step; scf_iters_host (may be
+ * NULL) receives the SCF iterations of each step.  The n history of the
+ * state holds the converged n afterwards; a following xlbomd_step
+ * re-evaluates its forces and kernel first. */
+int bomd_step(sxl_ctx* ctx, int nsteps, const sxl_scf_opts* opts, double tol, int max_iter,
+              double* stats_host, int* scf_iters_host);
+
 /* Diagnostic: C[b] = alpha A[b] B[b]^T + beta E[b] + gamma I (b = 0, 1; each
  * N x N, row-major fp64 device arrays, E may be NULL) through the library's
  * tensor-core GEMM, the product every step of the mixed-precision chains

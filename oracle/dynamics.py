@@ -153,3 +153,42 @@ class XLBOMD:
         return dict(Etot=self.E["U"] + ke, U=self.E["U"], KE=ke,
                     T=temperature(self.V, self.p.mass_amu),
                     rms=rms(self.dens.residual()), mu=self.mu)
+
+
+class BOMD:
+    """Regular Born-Oppenheimer MD, the comparison of Sec. IV: velocity
+    Verlet with the forces of the SCF ground state, the SCF at each step
+    started from the previous step's converged n and mixed with `mixer`
+    (scf above) to RMS(q - n) < tol."""
+
+    def __init__(self, R, V, cell, n0, p, tol=1e-8, mixer="diis", max_iter=400, mu=None):
+        self.p = p
+        self.cell = np.asarray(cell, dtype=np.float64)
+        self.R = np.array(R, dtype=np.float64)
+        self.V = np.array(V, dtype=np.float64)
+        self.tol, self.mixer, self.max_iter = tol, mixer, max_iter
+        self.n = np.array(n0, dtype=np.float64)
+        self.mu = mu
+        self.scf_iters = []
+        self._evaluate()
+
+    def _evaluate(self):
+        res = scf(self.R, self.cell, self.n, self.p, tol=self.tol, max_iter=self.max_iter,
+                  mixer=self.mixer)
+        self.n, self.mu, self.dens = res["n"], res["mu"], res["dens"]
+        self.scf_iters.append(res["iters"])
+        self.F = energy.forces(self.dens, self.R, self.cell)
+        H0 = model.build_h0(self.R, self.cell, self.p)
+        self.E = energy.shadow_energy(self.dens, H0,
+                                      model.repulsive_energy(self.R, self.cell, self.p))
+
+    def step(self):
+        dt = self.p.dt_fs
+        acc = self.F / (self.p.mass_amu * MVV_TO_EV)
+        self.V = self.V + 0.5 * dt * acc
+        self.R = self.R + dt * self.V
+        self._evaluate()
+        self.V = self.V + 0.5 * dt * self.F / (self.p.mass_amu * MVV_TO_EV)
+        ke = kinetic_energy(self.V, self.p.mass_amu)
+        return dict(Etot=self.E["U"] + ke, T=temperature(self.V, self.p.mass_amu),
+                    rms=rms(self.dens.residual()), mu=self.mu, scf_iters=self.scf_iters[-1])

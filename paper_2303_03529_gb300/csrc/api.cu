@@ -470,6 +470,10 @@ int sxl_create(const sxl_params* prm, void* stream, sxl_ctx** out) {
   c->N = NORB * p.n_atoms;
   c->Np = c->N;
   c->dup = nullptr;
+  c->diis_N = c->diis_F = c->diis_B = c->diis_coef = nullptr;
+  c->diis_list = c->diis_flag = nullptr;
+  c->diis_count = c->diis_head = 0;
+  c->bomd_ready = false;
   c->n2 = 2 * p.n_atoms;
   c->beta = 1.0 / p.kT;
   c->hist_head = 0;
@@ -532,6 +536,7 @@ int sxl_destroy(sxl_ctx* c) {
   for (double* p : c->T) cudaFree(p);
   for (double* p : c->Y) cudaFree(p);
   sxl_mixed_free(c);
+  diis_free(c);
   ev_resolve(c);
   for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
   if (c->hred) cudaFreeHost(c->hred);
@@ -672,6 +677,7 @@ static int set_state(sxl_ctx* c, const double* R, const double* V, const double*
   c->mu = mu;
   c->state_ready = true;
   c->evaluated = false;
+  c->bomd_ready = false;
   return SXL_OK;
 }
 
@@ -734,6 +740,7 @@ int xlbomd_step(sxl_ctx* c, int nsteps, double* stats) {
   if (!c || nsteps < 0) return SXL_E_ARG;
   if (!c->state_ready) return sxl_fail(c, SXL_E_STATE, "no MD state: call sxl_set_state first");
   if (!c->evaluated) SXL_TRY(evaluate(c, nullptr));
+  c->bomd_ready = false;
   const int K1 = c->p.kmax + 1;
   for (int s = 0; s < nsteps; ++s) {
     md_half_kick(c, c->V, c->F);
@@ -763,11 +770,29 @@ int xlbomd_step(sxl_ctx* c, int nsteps, double* stats) {
   return SXL_OK;
 }
 
-int scf_solve(sxl_ctx* c, const double* R, double* n, double tol, int max_iter, int* iters_out,
-              double* rms_out) {
-  if (!c || !R || !n || !(tol > 0) || max_iter < 1) return SXL_E_ARG;
-  bool k0 = false;
-  double mu = NAN, rms = 1e300;
+static sxl_scf_opts scf_defaults(const sxl_scf_opts* o) {
+  sxl_scf_opts d;
+  d.mixer = o ? o->mixer : SXL_MIX_KERNEL;
+  d.lin_mix = (o && o->lin_mix > 0) ? o->lin_mix : 0.06;
+  d.switch_rms = (o && o->switch_rms > 0) ? o->switch_rms : 0.05;
+  d.diis_hist = (o && o->diis_hist > 0) ? std::min(o->diis_hist, DIIS_MAX) : 8;
+  d.diis_mix = (o && o->diis_mix > 0) ? o->diis_mix : 0.1;
+  d.krylov_rel_tol = (o && o->krylov_rel_tol > 0) ? o->krylov_rel_tol : 0.1;
+  return d;
+}
+
+// SCF for q[n] = n at positions R (device), n updated in place.  Every
+// mixer starts with linear mixing n <- n + lin_mix (q - n); the kernel and
+// DIIS mixers take over once RMS(q - n) < switch_rms.  The kernel mixer is
+// the quasi-Newton step of Eq. QN with the preconditioned Krylov kernel of
+// Eq. mIJacobian (K0 = J^{-1} at the switch unless scf_keep_k0); DIIS is
+// Pulay's extrapolation over the last diis_hist pairs (scf.cu).
+static int scf_run(sxl_ctx* c, const double* R, double* n, double tol, int max_iter,
+                   const sxl_scf_opts& o, double* hist, int* iters_out, double* rms_out,
+                   double mu_guess) {
+  bool k0 = false, diis_on = false;
+  c->diis_count = c->diis_head = 0;
+  double mu = mu_guess, rms = 1e300;
   int it = 0;
   for (; it < max_iter; ++it) {
     c->have_density = false;
@@ -776,24 +801,87 @@ int scf_solve(sxl_ctx* c, const double* R, double* n, double tol, int max_iter, 
     rms_f64(c, c->n2, c->q, n, c->red + 102);
     SXL_TRY(sync_host(c, c->red + 102, 1));
     rms = c->hred[0];
+    if (hist) hist[it] = rms;
     if (!std::isfinite(rms)) return sxl_fail(c, SXL_E_NAN, "non-finite residual in SCF");
     if (rms < tol) break;
-    if (!k0 && rms >= 0.05) {
-      // linear mixing n <- n + 0.06 (q - n)
-      vec_axpby(c, c->n2, n, 0.94, n, 0.06, c->q);
+    const bool linear = o.mixer == SXL_MIX_LINEAR ||
+                        (o.mixer == SXL_MIX_DIIS && !diis_on && rms >= o.switch_rms) ||
+                        (o.mixer == SXL_MIX_KERNEL && !k0 && rms >= o.switch_rms);
+    if (linear) {
+      vec_axpby(c, c->n2, n, 1.0 - o.lin_mix, n, o.lin_mix, c->q);
+      continue;
+    }
+    if (o.mixer == SXL_MIX_DIIS) {
+      diis_on = true;
+      SXL_TRY(diis_step(c, n, o.diis_hist, o.diis_mix));
       continue;
     }
     if (!k0) {
       if (!c->p.scf_keep_k0) SXL_TRY(build_exact_k0(c, nullptr));
       k0 = true;
     }
-    SXL_TRY(krylov(c, n, c->p.krylov_rank, 0.1, c->Kf, nullptr, nullptr));
+    SXL_TRY(krylov(c, n, c->p.krylov_rank, o.krylov_rel_tol, c->Kf, nullptr, nullptr));
     vec_axpby(c, c->n2, n, 1.0, n, -1.0, c->Kf);
   }
   if (iters_out) *iters_out = it;
   if (rms_out) *rms_out = rms;
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   if (!(rms < tol)) return sxl_fail(c, SXL_E_NO_CONVERGENCE, "SCF hit max_iter");
+  return SXL_OK;
+}
+
+int scf_solve(sxl_ctx* c, const double* R, double* n, double tol, int max_iter, int* iters_out,
+              double* rms_out) {
+  if (!c || !R || !n || !(tol > 0) || max_iter < 1) return SXL_E_ARG;
+  return scf_run(c, R, n, tol, max_iter, scf_defaults(nullptr), nullptr, iters_out, rms_out, NAN);
+}
+
+int scf_solve_ex(sxl_ctx* c, const double* R, double* n, double tol, int max_iter,
+                 const sxl_scf_opts* opts, double* rms_hist, int* iters_out, double* rms_out) {
+  if (!c || !R || !n || !(tol > 0) || max_iter < 1) return SXL_E_ARG;
+  if (opts && (opts->mixer < SXL_MIX_KERNEL || opts->mixer > SXL_MIX_DIIS)) return SXL_E_ARG;
+  return scf_run(c, R, n, tol, max_iter, scf_defaults(opts), rms_hist, iters_out, rms_out, NAN);
+}
+
+// Regular BOMD for the comparison of Sec. IV: per step, velocity Verlet with
+// the forces of the SCF ground state at the new positions, the SCF started
+// from the previous step's converged n (the context's current n) and mixed
+// with opts (typically DIIS) to tol.
+int bomd_step(sxl_ctx* c, int nsteps, const sxl_scf_opts* opts, double tol, int max_iter,
+              double* stats, int* scf_iters) {
+  if (!c || nsteps < 0 || !(tol > 0) || max_iter < 1) return SXL_E_ARG;
+  if (!c->state_ready) return sxl_fail(c, SXL_E_STATE, "no MD state: call sxl_set_state first");
+  const sxl_scf_opts o = scf_defaults(opts);
+  double* n = c->nhist + (size_t)c->hist_head * c->n2;
+  if (!c->bomd_ready) {
+    int its = 0;
+    SXL_TRY(scf_run(c, c->R, n, tol, max_iter, o, nullptr, &its, nullptr, c->mu));
+    SXL_TRY(eval_forces(c, c->R, n, c->F, nullptr));
+    c->bomd_ready = true;
+  }
+  for (int s = 0; s < nsteps; ++s) {
+    md_half_kick(c, c->V, c->F);
+    md_drift(c, c->R, c->V);
+    int its = 0;
+    SXL_TRY(scf_run(c, c->R, n, tol, max_iter, o, nullptr, &its, nullptr, c->mu));
+    if (scf_iters) scf_iters[s] = its;
+    double en[6];
+    SXL_TRY(eval_forces(c, c->R, n, c->F, stats ? en : nullptr));
+    md_half_kick(c, c->V, c->F);
+    if (stats) {
+      md_kinetic(c, c->V, c->red + 100);
+      rms_f64(c, c->n2, c->q, n, c->red + 101);
+      SXL_TRY(sync_host(c, c->red + 100, 2));
+      double ke = c->hred[0];
+      stats[4 * s + 0] = en[0] + ke;
+      stats[4 * s + 1] = 2.0 * ke / ((3.0 * c->nat - 3.0) * KB_EV);
+      stats[4 * s + 2] = c->hred[1];
+      stats[4 * s + 3] = c->mu;
+    }
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  // the derived quantities of an sXL-BOMD step (F, Kf) are not current now
+  c->evaluated = false;
   return SXL_OK;
 }
 

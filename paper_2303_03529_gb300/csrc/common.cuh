@@ -77,6 +77,11 @@ struct sxl_ctx {
   bool teff_valid;        // hTeff (not hT[nr]) holds the final density
   double shift_tau;       // tanh(beta dmu / 2) of the exact shift in hTeff (0: none)
   double mu_prev;         // chemical potential of the previous MD step (NaN: none)
+  // DIIS history (scf.cu): rings of DIIS_MAX input / residual vectors
+  double *diis_N, *diis_F, *diis_B, *diis_coef;
+  int *diis_list, *diis_flag;
+  int diis_count, diis_head;
+  bool bomd_ready;        // F holds the SCF forces of the current state (bomd_step)
 
   double *diagT, *rowsq, *chi;  // 2N each
   double *du;                   // 2N perturbation (scaled) per orbital
@@ -191,6 +196,10 @@ int foe_mixed(sxl_ctx* c, double mu, double* stats_dev);
 int mu_shift_mixed(sxl_ctx* c, double dmu, double* stats_dev);
 int mu_shift_exact_mixed(sxl_ctx* c, double dmu, double* stats_dev);
 const MatH& final_T_mixed(const sxl_ctx* c);
+#define DIIS_MAX 16
+int diis_alloc(sxl_ctx* c);
+void diis_free(sxl_ctx* c);
+int diis_step(sxl_ctx* c, double* n, int hist, double mix);
 int dmpt_mixed(sxl_ctx* c, const double* du);
 void dot_h0_t_mixed(sxl_ctx* c, int spin, double* out);
 void density_matrix_mixed(sxl_ctx* c, double* D);

@@ -45,6 +45,15 @@ class Params(ctypes.Structure):
     ]
 
 
+MIXERS = {"kernel": 0, "linear": 1, "diis": 2}
+
+
+class ScfOpts(ctypes.Structure):
+    """Mirror of sxl_scf_opts (include/sxl.h)."""
+    _fields_ = [("mixer", _i), ("lin_mix", _d), ("switch_rms", _d), ("diis_hist", _i),
+                ("diis_mix", _d), ("krylov_rel_tol", _d)]
+
+
 EXPORTS = {
     "sxl_create": (_i, [ctypes.POINTER(Params), _p, ctypes.POINTER(_p)]),
     "sxl_destroy": (_i, [_p]),
@@ -63,6 +72,9 @@ EXPORTS = {
     "sxl_get_state_host": (_i, [_p, _p, _p, _p, ctypes.POINTER(_d)]),
     "xlbomd_step": (_i, [_p, _i, _p]),
     "scf_solve": (_i, [_p, _p, _p, _d, _i, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
+    "scf_solve_ex": (_i, [_p, _p, _p, _d, _i, ctypes.POINTER(ScfOpts), _p, ctypes.POINTER(_i),
+                          ctypes.POINTER(_d)]),
+    "bomd_step": (_i, [_p, _i, ctypes.POINTER(ScfOpts), _d, _i, _p, _p]),
     "sxl_info": (_i, [_p, _p]),
     "sxl_mixed_gemm": (_i, [_p, _p, _p, _p, _p, _d, _d, _d, _i, _i]),
     "sxl_set_derived_host": (_i, [_p, _p, _p]),
@@ -284,6 +296,37 @@ class Context:
                                        float(tol), int(max_iter), ctypes.byref(it),
                                        ctypes.byref(rms)), "scf_solve")
         return n, it.value, rms.value
+
+    @staticmethod
+    def _scf_opts(mixer="kernel", lin_mix=0.0, switch_rms=0.0, diis_hist=0, diis_mix=0.0,
+                  krylov_rel_tol=0.0):
+        return ScfOpts(MIXERS[mixer], float(lin_mix), float(switch_rms), int(diis_hist),
+                       float(diis_mix), float(krylov_rel_tol))
+
+    def scf_ex(self, R, n, tol=1e-8, max_iter=300, mixer="kernel", **opts):
+        """SCF with a choice of mixer ("kernel", "linear", "diis"); returns
+        (n, iterations, final RMS, RMS history as a numpy array)."""
+        R = self._dev(R)
+        n = self._dev(n).clone()
+        it, rms = _i(0), _d(0.0)
+        hist = np.zeros(int(max_iter))
+        o = self._scf_opts(mixer, **opts)
+        self._check(self.lib.scf_solve_ex(self.h, _ptr(R, 3 * self.nat), _ptr(n, self.n2),
+                                          float(tol), int(max_iter), ctypes.byref(o),
+                                          hist.ctypes.data_as(_p), ctypes.byref(it),
+                                          ctypes.byref(rms)), "scf_solve_ex")
+        return n, it.value, rms.value, hist[:it.value + 1].copy()
+
+    def bomd(self, nsteps=1, tol=1e-6, max_iter=200, mixer="diis", stats=True, **opts):
+        """Regular BOMD steps (SCF-converged forces); returns (stats, SCF
+        iterations per step)."""
+        out = np.zeros((max(nsteps, 1), 4)) if stats else None
+        its = np.zeros(max(nsteps, 1), dtype=np.int32)
+        o = self._scf_opts(mixer, **opts)
+        self._check(self.lib.bomd_step(self.h, int(nsteps), ctypes.byref(o), float(tol),
+                                       int(max_iter), out.ctypes.data_as(_p) if stats else None,
+                                       its.ctypes.data_as(_p)), "bomd_step")
+        return out, its[:nsteps].copy()
 
     def mixed_gemm(self, A, B, E=None, alpha=1.0, beta=0.0, gamma=0.0, sym=False, split=True):
         """C = alpha A B^T + beta E + gamma I on the tensor-core path (2 x N x N)."""

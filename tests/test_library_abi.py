@@ -58,3 +58,13 @@ def test_params_struct_matches_header():
         for item in parts[1].split(","):
             fields.append(item.strip().split("[")[0])
     assert fields == [f for f, _ in sxl.Params._fields_]
+
+
+def test_scf_opts_struct_matches_header():
+    from paper_2303_03529_gb300 import sxl
+    txt = open(os.path.join(ROOT, "include", "sxl.h")).read()
+    body = txt[txt.rindex("typedef struct {", 0, txt.index("} sxl_scf_opts;")):txt.index("} sxl_scf_opts;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S).replace("typedef struct {", "")
+    fields = [d.split()[-1] for d in body.split(";") if d.strip()]
+    assert fields == [f for f, _ in sxl.ScfOpts._fields_]
+    assert sxl.MIXERS == {"kernel": 0, "linear": 1, "diis": 2}

@@ -201,3 +201,28 @@ def test_shadow_energy_conservation_and_dt2_scaling():
     assert 2.5 < ratio_rms < 6.0
     assert 2.0 < ratio_e < 8.0
     assert out[0.5][0] / 16 < 1e-3   # eV/atom fluctuation bound over 20 fs
+
+
+def test_bomd_forces_are_minus_gradient_of_bo_energy():
+    """At the SCF fixed point U(R, n) is stationary in n, so the constant-n
+    forces of the converged state are -dE_BO/dR with E_BO(R) = U(R, n*(R))
+    (the property regular BOMD relies on).  Richardson-extrapolated central
+    differences of E_BO, each point converged with DIIS to 1e-11."""
+    w = wl.fe16()
+    p = w.params
+
+    def e_bo(R):
+        res = dynamics.scf(R, w.cell, w.n0, p, tol=1e-11, max_iter=600, mixer="diis")
+        H0 = model.build_h0(R, w.cell, p)
+        return energy.shadow_energy(res["dens"], H0, model.repulsive_energy(R, w.cell, p))["U"], res
+
+    _, res0 = e_bo(w.R)
+    F = energy.forces(res0["dens"], w.R, w.cell)
+    for (a, c) in ((0, 0), (5, 1), (11, 2)):
+        def d(h):
+            Rp, Rm = w.R.copy(), w.R.copy()
+            Rp[a, c] += h
+            Rm[a, c] -= h
+            return (e_bo(Rp)[0] - e_bo(Rm)[0]) / (2 * h)
+        g = (4 * d(1e-3) - d(2e-3)) / 3
+        assert abs(g + F[a, c]) < 1e-7, (a, c, g, F[a, c])
