@@ -223,6 +223,24 @@ int scf_solve_ex(sxl_ctx* ctx, const double* R_dev, double* n_dev, double tol, i
 int bomd_step(sxl_ctx* ctx, int nsteps, const sxl_scf_opts* opts, double tol, int max_iter,
               double* stats_host, int* scf_iters_host);
 
+/* Batched replicas (independent systems of any sizes; no counterpart in the
+ * paper beyond running its method on many cells).  sxl_batch_create makes
+ * `count` contexts from params[0..count-1], each on its own non-blocking
+ * stream created and owned by the batch; sxl_batch_context returns context
+ * i (owned by the batch: do not destroy it) for set_state / get_state and
+ * the other calls.  sxl_batch_step runs xlbomd_step(ctx_i, nsteps, NULL)
+ * for every replica on `nthreads` host threads (0 = min(count, 16)), the
+ * largest systems first; each replica's result is identical to stepping it
+ * alone.  status_host (may be NULL, count ints) receives each replica's
+ * return code; the call returns the first non-OK code (replica order), or
+ * SXL_OK.  A context must not be used from another thread while a batch
+ * step runs. */
+typedef struct sxl_batch sxl_batch;
+int sxl_batch_create(const sxl_params* params, int count, sxl_batch** out);
+int sxl_batch_context(sxl_batch* batch, int i, sxl_ctx** out);
+int sxl_batch_step(sxl_batch* batch, int nsteps, int nthreads, int* status_host);
+int sxl_batch_destroy(sxl_batch* batch);
+
 /* Diagnostic: C[b] = alpha A[b] B[b]^T + beta E[b] + gamma I (b = 0, 1; each
  * N x N, row-major fp64 device arrays, E may be NULL) through the library's
  * tensor-core GEMM, the product every step of the mixed-precision chains

@@ -953,7 +953,7 @@ int sxl_info(sxl_ctx* c, double* out) {
   out[3] = c->lam_min;
   out[4] = c->lam_max;
   out[5] = (double)c->n_gemm;
-  out[6] = (double)g_sxl_launches;
+  out[6] = (double)g_sxl_launches.load();
   return SXL_OK;
 }
 

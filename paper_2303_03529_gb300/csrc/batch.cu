@@ -1,0 +1,90 @@
+// Batched replicas: many independent systems (different sizes) stepped
+// together.  Each replica is an ordinary context on its own non-blocking
+// stream; a pool of host threads drives them, largest first, so the small
+// products of different replicas run on the GPU at the same time.  Replicas
+// share nothing but the device, so a batched step gives the same result, bit
+// for bit, as stepping the replica alone.
+#include "common.cuh"
+
+#include <algorithm>
+#include <thread>
+
+struct sxl_batch {
+  std::vector<sxl_ctx*> ctx;
+  std::vector<cudaStream_t> streams;
+  std::vector<int> order;  // replica indices, largest first
+};
+
+extern "C" {
+
+int sxl_batch_create(const sxl_params* params, int count, sxl_batch** out) {
+  if (!params || count < 1 || !out) return SXL_E_ARG;
+  *out = nullptr;
+  sxl_batch* b = new sxl_batch();
+  for (int i = 0; i < count; ++i) {
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      sxl_batch_destroy(b);
+      return SXL_E_CUDA;
+    }
+    b->streams.push_back(s);
+    sxl_ctx* c = nullptr;
+    int r = sxl_create(&params[i], (void*)s, &c);
+    if (r != SXL_OK) {
+      sxl_batch_destroy(b);
+      return r;
+    }
+    b->ctx.push_back(c);
+    b->order.push_back(i);
+  }
+  std::stable_sort(b->order.begin(), b->order.end(),
+                   [&](int x, int y) { return params[x].n_atoms > params[y].n_atoms; });
+  *out = b;
+  return SXL_OK;
+}
+
+int sxl_batch_context(sxl_batch* b, int i, sxl_ctx** out) {
+  if (!b || !out || i < 0 || i >= (int)b->ctx.size()) return SXL_E_ARG;
+  *out = b->ctx[i];
+  return SXL_OK;
+}
+
+int sxl_batch_step(sxl_batch* b, int nsteps, int nthreads, int* status) {
+  if (!b || nsteps < 0) return SXL_E_ARG;
+  const int count = (int)b->ctx.size();
+  if (nthreads <= 0) nthreads = std::min(count, 16);
+  nthreads = std::min(nthreads, count);
+  std::vector<int> rc(count, SXL_OK);
+  std::atomic<int> next{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SXL_E_CUDA;
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int k = next.fetch_add(1);
+      if (k >= count) break;
+      const int i = b->order[k];
+      rc[i] = xlbomd_step(b->ctx[i], nsteps, nullptr);
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 0; t < nthreads; ++t) pool.emplace_back(worker);
+  for (std::thread& t : pool) t.join();
+  int first = SXL_OK;
+  for (int i = 0; i < count; ++i) {
+    if (status) status[i] = rc[i];
+    if (first == SXL_OK && rc[i] != SXL_OK) first = rc[i];
+  }
+  return first;
+}
+
+int sxl_batch_destroy(sxl_batch* b) {
+  if (!b) return SXL_OK;
+  for (sxl_ctx* c : b->ctx) sxl_destroy(c);
+  for (cudaStream_t s : b->streams)
+    if (s) cudaStreamDestroy(s);
+  delete b;
+  return SXL_OK;
+}
+
+}  // extern "C"

@@ -4,6 +4,7 @@
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -15,7 +16,7 @@
 
 // Launch accounting: every kernel launch of the library goes through LAUNCH so
 // the host can report how many of its own kernels ran.
-extern unsigned long long g_sxl_launches;
+extern std::atomic<unsigned long long> g_sxl_launches;
 #define LAUNCH(kern, grid, block, smem, stream, ...)                 \
   do {                                                                \
     kern<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);        \

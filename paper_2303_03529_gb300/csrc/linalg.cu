@@ -7,7 +7,7 @@
 
 #include <cmath>
 
-unsigned long long g_sxl_launches = 0;
+std::atomic<unsigned long long> g_sxl_launches{0};
 
 // ---------------------------------------------------------------------------
 // GEMM, fp64: C = alpha A B^T + beta E + gamma I (square n x n, row-major,

@@ -472,11 +472,13 @@ static int make_map(sxl_ctx* c, CUtensorMap* m, const uint16_t* base, int n, int
 template <bool BF16, bool SPLIT, int BK, int MT = 1, bool DUAL = false>
 static int launch_tc(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a) {
   using Cfg = TcCfg<SPLIT, BK, MT>;
-  static bool attr = false;
-  if (!attr) {
+  // set once per instantiation (contexts may launch from several host threads;
+  // a repeated set is harmless)
+  static std::atomic<bool> attr{false};
+  if (!attr.load()) {
     CUDA_TRY(c, cudaFuncSetAttribute(k_tc_gemm<BF16, SPLIT, BK, MT, DUAL>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
-    attr = true;
+    attr.store(true);
   }
   dim3 grid(a.ntm * a.ntn, 2);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -515,19 +517,17 @@ int gemm_tc(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C, float alpha
   // K-block per product form (measured at n = 9216): split products run best
   // with 32-wide blocks (four 48 KB stages), plain ones with 64-wide blocks
   // (four 48 KB stages as well).  SXL_TC_BK=32 or 64 forces one width.
-  static int bk_env = -1;
-  if (bk_env < 0) {
+  static const int bk_env = [] {
     const char* e = getenv("SXL_TC_BK");
-    bk_env = e ? atoi(e) : 0;
-  }
+    return e ? atoi(e) : 0;
+  }();
   const int bk = (bk_env == 32 || bk_env == 64) ? bk_env : (split ? 32 : 64);
   // plain products cover 256 rows per CTA (two M = 128 MMAs per B tile);
   // SXL_TC_MT=1 restores 128-row tiles
-  static int mt_env = -1;
-  if (mt_env < 0) {
+  static const int mt_env = [] {
     const char* e = getenv("SXL_TC_MT");
-    mt_env = e ? atoi(e) : 0;
-  }
+    return e ? atoi(e) : 0;
+  }();
   const int mt = split ? 1 : (mt_env == 1 ? 1 : 2);
   CUtensorMap maps[4];
   SXL_TRY(make_map(c, &maps[0], A.hi, n, TC_BM * mt, bf16, bk));
@@ -1053,11 +1053,10 @@ int dmpt_mixed(sxl_ctx* c, const double* du_real) {
   // about 7e-4 (fp16) / 5e-3 (bf16) against 2e-5 / 1e-4 in the split form,
   // ample for the Krylov kernel, whose output only steers n.  SXL_DMPT_SPLIT=1
   // selects the split form.
-  static int use_split = -1;
-  if (use_split < 0) {
+  static const int use_split = [] {
     const char* e = getenv("SXL_DMPT_SPLIT");
-    use_split = (e && atoi(e) == 1) ? 1 : 0;
-  }
+    return (e && atoi(e) == 1) ? 1 : 0;
+  }();
   const bool split = use_split == 1;
   // the perturbation on the chain dimension (zero on the padding)
   double* du = c->dup;

@@ -75,6 +75,10 @@ EXPORTS = {
     "scf_solve_ex": (_i, [_p, _p, _p, _d, _i, ctypes.POINTER(ScfOpts), _p, ctypes.POINTER(_i),
                           ctypes.POINTER(_d)]),
     "bomd_step": (_i, [_p, _i, ctypes.POINTER(ScfOpts), _d, _i, _p, _p]),
+    "sxl_batch_create": (_i, [ctypes.POINTER(Params), _i, ctypes.POINTER(_p)]),
+    "sxl_batch_context": (_i, [_p, _i, ctypes.POINTER(_p)]),
+    "sxl_batch_step": (_i, [_p, _i, _i, _p]),
+    "sxl_batch_destroy": (_i, [_p]),
     "sxl_info": (_i, [_p, _p]),
     "sxl_mixed_gemm": (_i, [_p, _p, _p, _p, _p, _d, _d, _d, _i, _i]),
     "sxl_set_derived_host": (_i, [_p, _p, _p]),
@@ -434,3 +438,80 @@ def _host_ptr(a):
         return _p(a.data_ptr())
     a = np.ascontiguousarray(a, dtype=np.float64)
     return a.ctypes.data_as(_p)
+
+
+class _BatchContext(Context):
+    """A replica of a Batch: the context lives on a stream the batch owns, so
+    every call is bracketed by device synchronization (setup and inspection,
+    not the batched step)."""
+
+    def __init__(self, batch, handle, mp, n_atoms, cell, precision):
+        import torch
+        self.lib = batch.lib
+        self.nat = int(n_atoms)
+        self.N = 9 * self.nat
+        self.n2 = 2 * self.nat
+        self.kmax = int(mp.kmax)
+        self.params = make_params(mp, n_atoms, cell, precision)
+        self.stream = torch.cuda.current_stream()
+        self.h = handle
+        self._owned = False
+
+    def _dev(self, x):
+        import torch
+        t = super()._dev(x)
+        torch.cuda.synchronize()
+        return t
+
+    def _check(self, rc, what):
+        import torch
+        torch.cuda.synchronize()
+        super()._check(rc, what)
+
+    def close(self):
+        self.h = None   # owned by the batch
+
+
+class Batch:
+    """Independent replicas (any sizes) stepped together: one context per
+    replica on its own stream, driven by a pool of host threads."""
+
+    def __init__(self, workloads, precision="fp16", **kw):
+        self.lib = load_library()
+        self.workloads = list(workloads)
+        arr = (Params * len(self.workloads))()
+        for i, w in enumerate(self.workloads):
+            arr[i] = make_params(w.params, w.R.shape[0], w.cell, precision, **kw)
+        h = _p()
+        rc = self.lib.sxl_batch_create(arr, len(self.workloads), ctypes.byref(h))
+        if rc != 0:
+            raise SxlError(f"sxl_batch_create failed with code {rc}")
+        self.h = h
+        self.contexts = []
+        for i, w in enumerate(self.workloads):
+            c = _p()
+            if self.lib.sxl_batch_context(self.h, i, ctypes.byref(c)) != 0:
+                raise SxlError("sxl_batch_context failed")
+            self.contexts.append(_BatchContext(self, c, w.params, w.R.shape[0], w.cell, precision))
+
+    def step(self, nsteps=1, nthreads=0):
+        """nsteps sXL-BOMD steps of every replica; returns the per-replica
+        status codes (raises if any is not 0)."""
+        status = np.zeros(len(self.contexts), dtype=np.int32)
+        rc = self.lib.sxl_batch_step(self.h, int(nsteps), int(nthreads), status.ctypes.data_as(_p))
+        if rc != 0:
+            bad = [i for i, s in enumerate(status) if s != 0]
+            msgs = [self.lib.sxl_last_error(self.contexts[i].h).decode() for i in bad[:3]]
+            raise SxlError(f"sxl_batch_step failed ({rc}) for replicas {bad}: {msgs}")
+        return status
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sxl_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
