@@ -215,8 +215,8 @@ int scf_solve_ex(sxl_ctx* ctx, const double* R_dev, double* n_dev, double tol, i
  * SCF ground state at the new positions.  The SCF starts from the previous
  * step's converged n (the newest n of the state) and runs with opts to
  * RMS(q - n) < tol (at most max_iter iterations, else
- * SXL_E_NO_CONVERGENCE).  The first call converges the SCF at the initial
- * positions first.  stats_host as for xlbomd_step; scf_iters_host (may be
+ * SXL_E_NO_CONVERGENCE).  The first call with nsteps > 0 converges the SCF
+ * at the initial positions first; nsteps = 0 leaves the state as it is.  stats_host as for xlbomd_step; scf_iters_host (may be
  * NULL) receives the SCF iterations of each step.  The n history of the
  * state holds the converged n afterwards; a following xlbomd_step
  * re-evaluates its forces and kernel first. */

@@ -851,6 +851,7 @@ int bomd_step(sxl_ctx* c, int nsteps, const sxl_scf_opts* opts, double tol, int 
               double* stats, int* scf_iters) {
   if (!c || nsteps < 0 || !(tol > 0) || max_iter < 1) return SXL_E_ARG;
   if (!c->state_ready) return sxl_fail(c, SXL_E_STATE, "no MD state: call sxl_set_state first");
+  if (nsteps == 0) return SXL_OK;  // the state is left as it is
   const sxl_scf_opts o = scf_defaults(opts);
   double* n = c->nhist + (size_t)c->hist_head * c->n2;
   if (!c->bomd_ready) {

@@ -68,3 +68,35 @@ def test_scf_opts_struct_matches_header():
     fields = [d.split()[-1] for d in body.split(";") if d.strip()]
     assert fields == [f for f, _ in sxl.ScfOpts._fields_]
     assert sxl.MIXERS == {"kernel": 0, "linear": 1, "diis": 2}
+
+
+def test_create_rejects_bad_parameters_without_a_gpu(libpath):
+    """sxl_create checks its parameters before any CUDA call, so every
+    refusal can be checked on the CPU: SXL_E_ARG and no context."""
+    from dataclasses import replace
+
+    import numpy as np
+    from paper_2303_03529_gb300 import sxl
+    from paper_2303_03529_gb300 import workload as wl
+    lib = sxl.load_library(libpath)
+    w = wl.fe16()
+
+    def code(mp=None, n_atoms=16, cell=None, **kw):
+        p = sxl.make_params(mp or w.params, n_atoms, w.cell if cell is None else cell, **kw)
+        h = ctypes.c_void_p()
+        rc = lib.sxl_create(ctypes.byref(p), None, ctypes.byref(h))
+        assert not h.value
+        return rc
+
+    E_ARG = -1
+    assert code(n_atoms=1) == E_ARG                              # fewer than 2 atoms
+    assert code(cell=np.array([3.0, 5.74, 5.74])) == E_ARG       # 1.5 L <= r_cut
+    assert code(precision="fp16", foe_steps=41) == E_ARG
+    assert code(mp=replace(w.params, kmax=0)) == E_ARG
+    assert code(mp=replace(w.params, krylov_rank=0)) == E_ARG
+    assert code(mp=replace(w.params, n_elec_per_atom=0.0)) == E_ARG
+    assert code(mp=replace(w.params, kT=0.0)) == E_ARG
+    h = ctypes.c_void_p()
+    assert lib.sxl_batch_create(None, 0, ctypes.byref(h)) == E_ARG
+    assert lib.scf_solve_ex(None, None, None, 1e-8, 10, None, None, None, None) == E_ARG
+    assert lib.bomd_step(None, 1, None, 1e-8, 10, None, None) == E_ARG
