@@ -267,19 +267,34 @@ static int density(sxl_ctx* c, const double* R, const double* n, double mu_guess
     if (err > 0) hi = mu; else lo = mu;
     // mixed forms: the remaining shift of mu is applied to the final T by
     // the tanh addition theorem (one well-conditioned inverse instead of
-    // another expansion pass); a leftover of beta |dmu| <= 1e-2 is then
-    // applied to first order (neglected term <= (beta dmu)^2 / 20).
+    // another expansion pass), repeated with the accumulated shift until
+    // beta |dmu| <= 1e-2; that leftover is applied to first order (neglected
+    // term <= (beta dmu)^2 / 20).  The response follows both maps.
     if (mixed && dN > 0 && c->beta * std::fabs(err / dN) <= 1.0) {
-      double dmu = -err / dN;
-      if (c->beta * std::fabs(dmu) > 1e-2) {
-        SXL_TRY(mu_shift_exact_mixed(c, dmu, stats));
+      double dmu = -err / dN, total = 0.0;
+      bool done = false;
+      for (int e = 0; e < 4 && c->beta * std::fabs(dmu) > 1e-2; ++e) {
+        total += dmu;
+        SXL_TRY(mu_shift_exact_mixed(c, total, stats));
         SXL_TRY(sync_host(c, stats, 2));
-        mu += dmu;
         if (dbg)
-          fprintf(stderr, "[sxl] mu exact shift %.3e -> N %.10f\n", dmu, c->hred[0]);
-        double err2 = c->hred[0] - Ne;
+          fprintf(stderr, "[sxl] mu exact shift %.3e -> N %.10f\n", total, c->hred[0]);
+        const double err2 = c->hred[0] - Ne;
         dmu = (c->hred[1] > 0) ? -err2 / c->hred[1] : 0.0;
-        if (std::fabs(err2) < tol) { c->last_N = c->hred[0]; break; }
+        if (std::fabs(err2) < tol) {
+          c->last_N = c->hred[0];
+          done = true;
+          break;
+        }
+      }
+      mu += total;
+      if (done) break;
+      if (c->beta * std::fabs(dmu) > 1e-2) {
+        // the shifts did not settle: a full pass at the shifted mu
+        if (it + 1 >= maxit)
+          return sxl_fail(c, SXL_E_NO_CONVERGENCE, "chemical potential search hit its iteration cap");
+        mu += dmu;
+        continue;
       }
       SXL_TRY(mu_shift_mixed(c, dmu, stats));
       SXL_TRY(sync_host(c, stats, 2));
@@ -482,6 +497,7 @@ int sxl_create(const sxl_params* prm, void* stream, sxl_ctx** out) {
   c->teff_valid = false;
   c->apm_ready = false;
   c->shift_tau = 0.0;
+  c->fo_h = 0.0;
   c->fscratch = nullptr;
   c->state_ready = c->evaluated = c->have_density = c->h0_valid = false;
   c->nr = 0; c->nr_cap = 0;
@@ -502,6 +518,8 @@ int sxl_create(const sxl_params* prm, void* stream, sxl_ctx** out) {
   AL(R, 3 * nat); AL(V, 3 * nat); AL(F, 3 * nat); AL(Rcur, 3 * nat); AL(Fband, 3 * nat);
   AL(nhist, (size_t)K1 * n2); AL(Kf, n2); AL(q, n2); AL(fres, n2); AL(tmpv, std::max(n2, 3 * nat));
   AL(gamma_m, (size_t)nat * nat); AL(H0, (size_t)N * N); AL(h0abs, N); AL(shift, 2 * nat);
+  if (r == SXL_OK && cudaMalloc((void**)&c->H0f, (size_t)N * N * sizeof(float)) != cudaSuccess)
+    r = SXL_E_NOMEM;
   if (p.precision == SXL_FP64) {
     AL(U, mm); AL(S, mm); AL(Q, mm); AL(X0, mm); AL(X1, mm); AL(P, mm); AL(Sm, mm);
     AL(dTa, mm); AL(dTb, mm); AL(G1, mm);
@@ -533,6 +551,7 @@ int sxl_destroy(sxl_ctx* c) {
                     c->Jinv};
   for (double* p : ptrs)
     if (p) cudaFree(p);
+  if (c->H0f) cudaFree(c->H0f);
   for (double* p : c->T) cudaFree(p);
   for (double* p : c->Y) cudaFree(p);
   sxl_mixed_free(c);

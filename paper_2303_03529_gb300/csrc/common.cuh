@@ -49,6 +49,7 @@ struct sxl_ctx {
   double *Rcur;           // positions of the current H0
   double *gamma_m;        // N_at x N_at
   double *H0;             // N x N
+  float *H0f;             // N x N, fp32 copy for the Lanczos bounds
   double *h0abs;          // N: sum_{j != i} |H0_ij|
   double *shift;          // 2 x N_at per-atom diagonal shifts h_sigma
   double *Fband;          // scratch force
@@ -77,6 +78,7 @@ struct sxl_ctx {
   float* fscratch;        // 2 Np^2 fp32 (entropy factorizations, mixed forms)
   bool teff_valid;        // hTeff (not hT[nr]) holds the final density
   double shift_tau;       // tanh(beta dmu / 2) of the exact shift in hTeff (0: none)
+  double fo_h;            // h = beta dmu / 2 of a first-order shift on top (0: none)
   double mu_prev;         // chemical potential of the previous MD step (NaN: none)
   // DIIS history (scf.cu): rings of DIIS_MAX input / residual vectors
   double *diis_N, *diis_F, *diis_B, *diis_coef;

@@ -664,8 +664,10 @@ void energy_terms(sxl_ctx* c, const double* n, const double* erep_atom, double* 
 #define LZ 32
 // w[s] = H_s v[s] - beta_prev v_prev[s]; partial alpha = v . w  (warp per row)
 // w_s = H_s v_s - beta_s vprev_s for both spins (H_s = H0 + diagonal
-// shift), one warp per row of H0, which is read once for the two spins
-__global__ void k_lz_matvec(int nat, const double* __restrict__ H0, const double* __restrict__ shift,
+// shift), one warp per row of H0, which is read once for the two spins, in
+// fp32 (the bounds carry a margin of at least 1 eV; the products and lane sums
+// are good to ~1e-6 relative)
+__global__ void k_lz_matvec(int nat, const float* __restrict__ H0, const double* __restrict__ shift,
                             const double* __restrict__ v, const double* __restrict__ vprev,
                             const double* __restrict__ beta, double* w) {
   const int N = nat * NORB;
@@ -674,12 +676,13 @@ __global__ void k_lz_matvec(int nat, const double* __restrict__ H0, const double
   if (i >= N) return;
   const double* v0 = v;
   const double* v1 = v + N;
-  double a0 = 0.0, a1 = 0.0;
+  float f0 = 0.f, f1 = 0.f;
   for (int j = lane; j < N; j += 32) {
-    const double h = H0[(size_t)i * N + j];
-    a0 += h * v0[j];
-    a1 += h * v1[j];
+    const float h = H0[(size_t)i * N + j];
+    f0 = fmaf(h, (float)v0[j], f0);
+    f1 = fmaf(h, (float)v1[j], f1);
   }
+  double a0 = f0, a1 = f1;
   for (int o = 16; o > 0; o >>= 1) {
     a0 += __shfl_down_sync(0xffffffffu, a0, o);
     a1 += __shfl_down_sync(0xffffffffu, a1, o);
@@ -828,7 +831,7 @@ void lanczos_bounds(sxl_ctx* c, double* out2) {
   LAUNCH(k_lz_normalize, 2, 1024, 0, c->st, N, v);
   int wpb = 8;
   for (int it = 0; it < LZ; ++it) {
-    LAUNCH(k_lz_matvec, (N + wpb - 1) / wpb, 32 * wpb, 0, c->st, c->nat, c->H0, c->shift, v,
+    LAUNCH(k_lz_matvec, (N + wpb - 1) / wpb, 32 * wpb, 0, c->st, c->nat, c->H0f, c->shift, v,
            vprev, beta, w);
     LAUNCH(k_lz_update, 2, 1024, 0, c->st, N, it, v, vprev, w, beta, al, be);
   }

@@ -177,6 +177,34 @@ __device__ __forceinline__ double ld_hl_d(const uint16_t* hi, const uint16_t* lo
 }
 // store v as (hi, lo): both parts carry at most 22 significant bits together,
 // so fp32 (24 bits) is exact enough for the split
+// eight consecutive (hi, lo) values from 16-byte loads (i % 8 == 0)
+template <bool BF16>
+__device__ __forceinline__ void ld8(const uint16_t* hi, const uint16_t* lo, size_t i, float v[8]) {
+  const uint4 h = *reinterpret_cast<const uint4*>(hi + i);
+  const uint4 l = *reinterpret_cast<const uint4*>(lo + i);
+  const uint32_t hw[4] = {h.x, h.y, h.z, h.w}, lw[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[2 * k] = HL<BF16>::f((uint16_t)(hw[k] & 0xffffu)) + HL<BF16>::f((uint16_t)(lw[k] & 0xffffu)) * LO_INV;
+    v[2 * k + 1] = HL<BF16>::f((uint16_t)(hw[k] >> 16)) + HL<BF16>::f((uint16_t)(lw[k] >> 16)) * LO_INV;
+  }
+}
+// eight values to (hi, lo) with 16-byte stores (i % 8 == 0)
+template <bool BF16>
+__device__ __forceinline__ void st8(uint16_t* hi, uint16_t* lo, size_t i, const float v[8]) {
+  uint32_t hw[4], lw[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint16_t h0 = HL<BF16>::b(v[2 * k]), h1 = HL<BF16>::b(v[2 * k + 1]);
+    const uint16_t l0 = HL<BF16>::b((v[2 * k] - HL<BF16>::f(h0)) * LO_SCALE);
+    const uint16_t l1 = HL<BF16>::b((v[2 * k + 1] - HL<BF16>::f(h1)) * LO_SCALE);
+    hw[k] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+    lw[k] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+  }
+  *reinterpret_cast<uint4*>(hi + i) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+  *reinterpret_cast<uint4*>(lo + i) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+}
+
 template <bool BF16>
 __device__ __forceinline__ void st_hl(uint16_t* hi, uint16_t* lo, size_t i, float v) {
   uint16_t h = HL<BF16>::b(v);
@@ -624,17 +652,21 @@ __global__ void k_build_u_h(int nat, int np, const double* __restrict__ H0,
 template <bool BF16>
 __global__ void k_rowstats_h(int np, int n, const uint16_t* hi, const uint16_t* lo, double* diag,
                              double* rowsq) {
-  // rows of the n real orbitals of both spins (matrices np x np); outputs
-  // indexed by spin * n + row
+  // rows of the n real orbitals of both spins (matrices np x np, np % 8 == 0);
+  // outputs indexed by spin * n + row; eight values per lane and load, fp64
+  // squares and sums (chi needs 1 - sum_j T_ij^2, which cancels for nearly
+  // saturated orbitals)
   int row = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   int lane = threadIdx.x & 31;
   if (row >= 2 * n) return;
   int b = row / n, i = row % n;
   size_t base = (size_t)b * np * np + (size_t)i * np;
   double s = 0.0;
-  for (int j = lane; j < np; j += 32) {
-    double t = ld_hl_d<BF16>(hi, lo, base + j);
-    s += t * t;
+  for (int j = 8 * lane; j < np; j += 256) {
+    float v[8];
+    ld8<BF16>(hi, lo, base + j, v);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s = fma((double)v[k], (double)v[k], s);
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   if (lane == 0) {
@@ -770,24 +802,26 @@ static void symcombo_h(sxl_ctx* c, const MatH& out, double a, const MatH* X, dou
 }
 
 template <bool BF16>
-__global__ void k_axpy_diag2_h(size_t pairs, int n, uint16_t* ohi, uint16_t* olo, float a,
+__global__ void k_axpy_diag2_h(size_t groups, int n, uint16_t* ohi, uint16_t* olo, float a,
                                const uint16_t* xhi, const uint16_t* xlo, float g) {
-  size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (p >= pairs) return;
-  size_t i = 2 * p;
-  size_t e = i % ((size_t)n * n);
-  float v0, v1;
-  ld_pair<BF16>(xhi, xlo, i, v0, v1);
-  v0 *= a;
-  v1 *= a;
-  if (e / n == e % n) v0 += g;            // n even: the diagonal element is
-  if ((e + 1) / n == (e + 1) % n) v1 += g;  // either of the pair
-  st_pair<BF16>(ohi, olo, i, v0, v1);
+  // out = a X + g I on both spins, eight elements per thread (n % 8 == 0, so
+  // a group lies in one row and holds that row's diagonal element or none)
+  size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= groups) return;
+  const size_t i = 8 * t;
+  const size_t e = i % ((size_t)n * n);
+  const size_t r = e / n, c0 = e % n;
+  float v[8];
+  ld8<BF16>(xhi, xlo, i, v);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] *= a;
+  if (r >= c0 && r < c0 + 8) v[r - c0] += g;
+  st8<BF16>(ohi, olo, i, v);
 }
 
 static void axpy_diag_h(sxl_ctx* c, const MatH& out, double a, const MatH& X, double g) {
-  size_t pairs = (size_t)c->Np * c->Np;  // 2 spins x Np^2 / 2
-  DISPATCH(c, k_axpy_diag2_h, (unsigned)((pairs + 255) / 256), 256, 0, pairs, c->Np, out.hi,
+  size_t groups = (size_t)c->Np * c->Np / 4;  // 2 spins x Np^2 / 8
+  DISPATCH(c, k_axpy_diag2_h, (unsigned)((groups + 255) / 256), 256, 0, groups, c->Np, out.hi,
            out.lo, (float)a, X.hi, X.lo, (float)g);
 }
 
@@ -802,8 +836,14 @@ __global__ void k_rowdot2_h(int np, int n, const uint16_t* ahi, const uint16_t* 
   int b = row / n, i = row % n;
   size_t base = (size_t)b * np * np + (size_t)i * np;
   double acc = 0.0;
-  for (int j = lane; j < np; j += 32)
-    acc += (double)ld_hl<BF16>(ahi, alo, base + j) * (double)ld_hl<BF16>(bhi, blo, base + j);
+  for (int j = 8 * lane; j < np; j += 256) {
+    // fp64 products: the terms of a diagonal element of dT cancel strongly
+    float x[8], y[8];
+    ld8<BF16>(ahi, alo, base + j, x);
+    ld8<BF16>(bhi, blo, base + j, y);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc = fma((double)x[k], (double)y[k], acc);
+  }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if (lane == 0) out[row] = scale * acc;
 }
@@ -938,6 +978,7 @@ int foe_mixed(sxl_ctx* c, double mu, double* stats_dev) {
   const double tol = 1e-7;
   c->teff_valid = false;
   c->shift_tau = 0.0;
+  c->fo_h = 0.0;
   c->apm_ready = false;
   c->ns_iters.assign(nr, 0);
   for (int k = 0; k < nr; ++k) {
@@ -1015,6 +1056,7 @@ int mu_shift_exact_mixed(sxl_ctx* c, double dmu, double* stats_dev) {
   std::swap(c->hXs, cur == &c->hX0 ? c->hX0 : c->hX1);
   c->teff_valid = true;
   c->shift_tau = tau;
+  c->fo_h = 0.0;
   int wpb = 8, rows = 2 * N;
   DISPATCH(c, k_rowstats_h, (rows + wpb - 1) / wpb, 32 * wpb, 0, c->Np, N, c->hTeff.hi,
            c->hTeff.lo, c->diagT, c->rowsq);
@@ -1039,6 +1081,7 @@ int mu_shift_mixed(sxl_ctx* c, double dmu, double* stats_dev) {
     SXL_TRY(gemm_tc(c, T, T, c->hTeff, h, &T, 1.f, -h, true, true));
   }
   c->teff_valid = true;
+  c->fo_h = 0.5 * c->beta * dmu;
   int wpb = 8, rows = 2 * N;
   DISPATCH(c, k_rowstats_h, (rows + wpb - 1) / wpb, 32 * wpb, 0, c->Np, N, c->hTeff.hi,
            c->hTeff.lo, c->diagT, c->rowsq);
@@ -1076,17 +1119,36 @@ int dmpt_mixed(sxl_ctx* c, const double* du_real) {
   //   dT_{k+1} = A- dT A+ + A+ dT A- = A- V^T + V A-,  V = A+ dT.
   // One full product and one symmetric product over [A- | V][V | A-]^T per
   // step (the three-product form needs half a product more).
+  const bool shifted = c->teff_valid && c->shift_tau != 0.0;
   if (!c->apm_ready) {
     const size_t pairs = (size_t)Np * Np;
     for (int k = 0; k < nr; ++k)
       DISPATCH(c, k_apm_h, (unsigned)((pairs + 255) / 256), 256, 0, pairs, c->hY[k].hi,
                c->hY[k].lo, c->hT[k + 1].hi, c->hT[k + 1].lo, c->hAm[k].hi, c->hAm[k].lo);
+    // A first-order shift T_eff = T + h (T^2 - I) after the chain maps
+    // dT -> dT + h (T dT + dT T) = (I + h T) dT (I + h T) + O(h^2): it folds
+    // into the last operators, A+- -> (I + h T_nr) A+-, or, after an exact
+    // shift, X -> (I + h T') X (T' ~ T_eff to O(h)).  Products of commuting
+    // matrices: symmetric outputs.
+    if (c->fo_h != 0.0) {
+      const float h = (float)c->fo_h;
+      if (!shifted) {
+        MatH& Ap = c->hY[nr - 1];
+        MatH& Am = c->hAm[nr - 1];
+        SXL_TRY(gemm_tc(c, c->hT[nr], Ap, c->hX0, h, &Ap, 1.f, 0.f, true, false));
+        SXL_TRY(gemm_tc(c, c->hT[nr], Am, c->hX1, h, &Am, 1.f, 0.f, true, false));
+        std::swap(Ap, c->hX0);
+        std::swap(Am, c->hX1);
+      } else {
+        SXL_TRY(gemm_tc(c, c->hTeff, c->hXs, c->hX0, h, &c->hXs, 1.f, 0.f, true, true));
+        std::swap(c->hXs, c->hX0);
+      }
+    }
     c->apm_ready = true;
   }
   // Only diag(dT_nr) is needed (q_v): the last step ends in row dots,
   // diag(A- V^T + V A-) = 2 rowdot(A-, V), and with an exact shift the map
   // (1 - tau^2) X dT X ends in diag(X dT X) = rowdot(X dT, X).
-  const bool shifted = c->teff_valid && c->shift_tau != 0.0;
   const int wpb = 8;
   for (int k = 0; k < nr; ++k) {
     SXL_TRY(gemm_tc(c, c->hY[k], *dA, c->hG1, 1.f, nullptr, 0.f, 0.f, false, split));
@@ -1105,8 +1167,9 @@ int dmpt_mixed(sxl_ctx* c, const double* du_real) {
     std::swap(dA, dB);
   }
   // the final T was shifted exactly (tanh addition): the same map carries
-  // the response, dT' = (1 - tau^2) X dT X with X = (I - tau T)^{-1}
-  SXL_TRY(gemm_tc(c, c->hXs, *dA, c->hG1, 1.f, nullptr, 0.f, 0.f, false, split));
+  // the response, dT' = (1 - tau^2) X dT X with X = (I - tau T)^{-1}.  X has
+  // entries up to 1 / (1 - |tau|), so this one product runs in split form.
+  SXL_TRY(gemm_tc(c, c->hXs, *dA, c->hG1, 1.f, nullptr, 0.f, 0.f, false, true));
   DISPATCH(c, k_rowdot2_h, (2 * N + wpb - 1) / wpb, 32 * wpb, 0, Np, N, c->hG1.hi, c->hG1.lo,
            c->hXs.hi, c->hXs.lo, 1.0 - c->shift_tau * c->shift_tau, c->diagT + 2 * N);
   return SXL_OK;

@@ -156,7 +156,7 @@ __device__ inline double min_image(double d, double L) { return d - L * rint(d /
 // are unrolled (the key of every lane is the same, so the Slater-Koster
 // cases do not diverge) and the lower ones follow by parity.
 __global__ void k_build_h0(int nat, const double* __restrict__ R, ModelConst mc,
-                           double* __restrict__ H0) {
+                           double* __restrict__ H0, float* __restrict__ H0f) {
   const int K = blockIdx.x;
   const int N = nat * NORB;
   const double Kx = R[3 * K], Ky = R[3 * K + 1], Kz = R[3 * K + 2];
@@ -186,6 +186,9 @@ __global__ void k_build_h0(int nat, const double* __restrict__ R, ModelConst mc,
           if (b != a) blk[(size_t)b * N + a] += ((c_ell[a] + c_ell[b]) & 1) ? -e : e;
         }
     }
+    float* blkf = H0f + (size_t)(NORB * K) * N + NORB * J;
+    for (int a = 0; a < NORB; ++a)
+      for (int b = 0; b < NORB; ++b) blkf[(size_t)a * N + b] = (float)blk[(size_t)a * N + b];
   }
 }
 
@@ -203,7 +206,7 @@ __global__ void k_rowabs(int N, const double* __restrict__ H0, double* __restric
 
 void launch_build_h0(sxl_ctx* c, const double* R) {
   ModelConst mc = model_const(c->p);
-  LAUNCH(k_build_h0, c->nat, 256, 0, c->st, c->nat, R, mc, c->H0);
+  LAUNCH(k_build_h0, c->nat, 256, 0, c->st, c->nat, R, mc, c->H0, c->H0f);
   int wpb = 8;
   LAUNCH(k_rowabs, (c->N + wpb - 1) / wpb, 32 * wpb, 0, c->st, c->N, c->H0, c->h0abs);
 }
