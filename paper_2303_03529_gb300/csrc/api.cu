@@ -265,37 +265,11 @@ static int density(sxl_ctx* c, const double* R, const double* n, double mu_guess
     if (it + 1 >= maxit)
       return sxl_fail(c, SXL_E_NO_CONVERGENCE, "chemical potential search hit its iteration cap");
     if (err > 0) hi = mu; else lo = mu;
-    // mixed forms: the remaining shift of mu is applied to the final T by
-    // the tanh addition theorem (one well-conditioned inverse instead of
-    // another expansion pass), repeated with the accumulated shift until
-    // beta |dmu| <= 1e-2; that leftover is applied to first order (neglected
-    // term <= (beta dmu)^2 / 20).  The response follows both maps.
-    if (mixed && dN > 0 && c->beta * std::fabs(err / dN) <= 1.0) {
-      double dmu = -err / dN, total = 0.0;
-      bool done = false;
-      for (int e = 0; e < 4 && c->beta * std::fabs(dmu) > 1e-2; ++e) {
-        total += dmu;
-        SXL_TRY(mu_shift_exact_mixed(c, total, stats));
-        SXL_TRY(sync_host(c, stats, 2));
-        if (dbg)
-          fprintf(stderr, "[sxl] mu exact shift %.3e -> N %.10f\n", total, c->hred[0]);
-        const double err2 = c->hred[0] - Ne;
-        dmu = (c->hred[1] > 0) ? -err2 / c->hred[1] : 0.0;
-        if (std::fabs(err2) < tol) {
-          c->last_N = c->hred[0];
-          done = true;
-          break;
-        }
-      }
-      mu += total;
-      if (done) break;
-      if (c->beta * std::fabs(dmu) > 1e-2) {
-        // the shifts did not settle: a full pass at the shifted mu
-        if (it + 1 >= maxit)
-          return sxl_fail(c, SXL_E_NO_CONVERGENCE, "chemical potential search hit its iteration cap");
-        mu += dmu;
-        continue;
-      }
+    // mixed forms: a remaining Newton step with beta |dmu| <= 1e-2 is
+    // applied to the final T to first order (neglected term <= (beta dmu)^2
+    // / 20) instead of another pass; the response follows it.
+    if (mixed && dN > 0 && c->beta * std::fabs(err / dN) <= 1e-2) {
+      const double dmu = -err / dN;
       SXL_TRY(mu_shift_mixed(c, dmu, stats));
       SXL_TRY(sync_host(c, stats, 2));
       mu += dmu;
@@ -496,7 +470,6 @@ int sxl_create(const sxl_params* prm, void* stream, sxl_ctx** out) {
   c->mu_prev = NAN;
   c->teff_valid = false;
   c->apm_ready = false;
-  c->shift_tau = 0.0;
   c->fo_h = 0.0;
   c->fscratch = nullptr;
   c->state_ready = c->evaluated = c->have_density = c->h0_valid = false;

@@ -74,11 +74,9 @@ struct sxl_ctx {
   std::vector<MatH> hAm;  // Y_k - T_{k+1}/2 (response form; hY[k] then holds Y_k + T_{k+1}/2)
   bool apm_ready;         // hY / hAm hold the response operators of the current chain
   MatH hTeff;             // T_nr after a first-order chemical-potential shift
-  MatH hXs;               // (I - tau T_nr)^{-1} of the last exact shift
   float* fscratch;        // 2 Np^2 fp32 (entropy factorizations, mixed forms)
   bool teff_valid;        // hTeff (not hT[nr]) holds the final density
-  double shift_tau;       // tanh(beta dmu / 2) of the exact shift in hTeff (0: none)
-  double fo_h;            // h = beta dmu / 2 of a first-order shift on top (0: none)
+  double fo_h;            // h = beta dmu / 2 of the first-order shift in hTeff (0: none)
   double mu_prev;         // chemical potential of the previous MD step (NaN: none)
   // DIIS history (scf.cu): rings of DIIS_MAX input / residual vectors
   double *diis_N, *diis_F, *diis_B, *diis_coef;
@@ -197,7 +195,6 @@ int sxl_mixed_supported(sxl_ctx* c);
 void sxl_mixed_free(sxl_ctx* c);
 int foe_mixed(sxl_ctx* c, double mu, double* stats_dev);
 int mu_shift_mixed(sxl_ctx* c, double dmu, double* stats_dev);
-int mu_shift_exact_mixed(sxl_ctx* c, double dmu, double* stats_dev);
 const MatH& final_T_mixed(const sxl_ctx* c);
 #define DIIS_MAX 16
 int diis_alloc(sxl_ctx* c);

@@ -664,34 +664,48 @@ void energy_terms(sxl_ctx* c, const double* n, const double* erep_atom, double* 
 #define LZ 32
 // w[s] = H_s v[s] - beta_prev v_prev[s]; partial alpha = v . w  (warp per row)
 // w_s = H_s v_s - beta_s vprev_s for both spins (H_s = H0 + diagonal
-// shift), one warp per row of H0, which is read once for the two spins, in
-// fp32 (the bounds carry a margin of at least 1 eV; the products and lane sums
-// are good to ~1e-6 relative)
+// shift).  One warp per LZ_ROWS rows of H0, read once for the two spins, so
+// each load of v serves LZ_ROWS rows; fp32 products and lane sums (the
+// bounds carry a margin of at least 1 eV; the sums are good to ~1e-6
+// relative).
+#define LZ_ROWS 4
 __global__ void k_lz_matvec(int nat, const float* __restrict__ H0, const double* __restrict__ shift,
                             const double* __restrict__ v, const double* __restrict__ vprev,
                             const double* __restrict__ beta, double* w) {
   const int N = nat * NORB;
-  int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  int lane = threadIdx.x & 31;
-  if (i >= N) return;
+  const int i0 = (blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32) * LZ_ROWS;
+  const int lane = threadIdx.x & 31;
+  if (i0 >= N) return;
   const double* v0 = v;
   const double* v1 = v + N;
-  float f0 = 0.f, f1 = 0.f;
+  float f0[LZ_ROWS], f1[LZ_ROWS];
+#pragma unroll
+  for (int r = 0; r < LZ_ROWS; ++r) f0[r] = f1[r] = 0.f;
   for (int j = lane; j < N; j += 32) {
-    const float h = H0[(size_t)i * N + j];
-    f0 = fmaf(h, (float)v0[j], f0);
-    f1 = fmaf(h, (float)v1[j], f1);
+    const float x0 = (float)v0[j], x1 = (float)v1[j];
+#pragma unroll
+    for (int r = 0; r < LZ_ROWS; ++r) {
+      if (i0 + r < N) {
+        const float h = H0[(size_t)(i0 + r) * N + j];
+        f0[r] = fmaf(h, x0, f0[r]);
+        f1[r] = fmaf(h, x1, f1[r]);
+      }
+    }
   }
-  double a0 = f0, a1 = f1;
-  for (int o = 16; o > 0; o >>= 1) {
-    a0 += __shfl_down_sync(0xffffffffu, a0, o);
-    a1 += __shfl_down_sync(0xffffffffu, a1, o);
-  }
-  if (lane == 0) {
-    a0 += shift[i / NORB] * v0[i];
-    a1 += shift[nat + i / NORB] * v1[i];
-    w[i] = a0 - beta[0] * vprev[i];
-    w[N + i] = a1 - beta[1] * vprev[N + i];
+#pragma unroll
+  for (int r = 0; r < LZ_ROWS; ++r) {
+    double a0 = f0[r], a1 = f1[r];
+    for (int o = 16; o > 0; o >>= 1) {
+      a0 += __shfl_down_sync(0xffffffffu, a0, o);
+      a1 += __shfl_down_sync(0xffffffffu, a1, o);
+    }
+    const int i = i0 + r;
+    if (lane == 0 && i < N) {
+      a0 += shift[i / NORB] * v0[i];
+      a1 += shift[nat + i / NORB] * v1[i];
+      w[i] = a0 - beta[0] * vprev[i];
+      w[N + i] = a1 - beta[1] * vprev[N + i];
+    }
   }
 }
 
@@ -831,7 +845,8 @@ void lanczos_bounds(sxl_ctx* c, double* out2) {
   LAUNCH(k_lz_normalize, 2, 1024, 0, c->st, N, v);
   int wpb = 8;
   for (int it = 0; it < LZ; ++it) {
-    LAUNCH(k_lz_matvec, (N + wpb - 1) / wpb, 32 * wpb, 0, c->st, c->nat, c->H0f, c->shift, v,
+    LAUNCH(k_lz_matvec, (N + wpb * LZ_ROWS - 1) / (wpb * LZ_ROWS), 32 * wpb, 0, c->st, c->nat,
+           c->H0f, c->shift, v,
            vprev, beta, w);
     LAUNCH(k_lz_update, 2, 1024, 0, c->st, N, it, v, vprev, w, beta, al, be);
   }

@@ -223,6 +223,7 @@ struct TcArgs {
   uint16_t* Clo;
   int sym;
   int* err;
+  int kb0 = 0;  // first k block of this launch (a product split over K)
 };
 
 // MT = 2 (plain products only): the CTA covers 256 output rows as two
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(192, 1)
           tma_load_2d(st + Cfg::A_BYTES, &mBl, fb, kx, bz * g.n + col0);
           continue;
         }
-        const int kx = kb * BK;
+        const int kx = (kb + g.kb0) * BK;
         tma_load_2d(st, &mAh, fb, kx, bz * g.n + row0);
         tma_load_2d(st + Cfg::A_BYTES, &mBh, fb, kx, bz * g.n + col0);
         if (SPLIT) {
@@ -525,12 +526,11 @@ static int launch_tc(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a) {
     for (int tm = 0; tm < a.ntm; ++tm)
       for (int tn = 0; tn < a.ntn; ++tn)
         if (!a.sym || tn * TC_BN + TC_BN - 1 >= tm * TC_BM * MT) tiles += 1;
-    double n = a.n;
-    double mma = 2.0 * tiles * 2.0 * TC_BM * MT * TC_BN * n * (SPLIT ? 3.0 : 1.0);
-    const double kfac = DUAL ? 2.0 : 1.0;  // dual products run over 2n
-    mma *= kfac;
-    double owned = a.sym ? n * (n + 1) / 2 : n * n;
-    double f32 = 2.0 * 2.0 * owned * n * kfac;  // both spins, 2 n (4 n dual) per owned element
+    const double n = a.n;
+    const double kdim = (double)a.nk * BK;  // this launch's K (2n for dual products)
+    const double mma = 2.0 * tiles * 2.0 * TC_BM * MT * TC_BN * kdim * (SPLIT ? 3.0 : 1.0);
+    const double owned = a.sym ? n * (n + 1) / 2 : n * n;
+    const double f32 = 2.0 * 2.0 * owned * kdim;  // both spins, 2 K per owned element
     c->ev_pending.push_back({e0, e1, mma, f32 * (SPLIT ? 3.0 : 1.0), f32});
   }
   return SXL_OK;
@@ -538,18 +538,24 @@ static int launch_tc(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a) {
 
 // C = alpha A B^T + beta E + gamma I for both spins; split selects the
 // three-product form.  Matrices are n x n with n % 64 == 0.
-int gemm_tc(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C, float alpha,
-            const MatH* E, float beta, float gamma, bool sym, bool split) {
-  const bool bf16 = c->p.precision == SXL_MIXED_BF16;
-  const int n = c->Np;
-  // K-block per product form (measured at n = 9216): split products run best
-  // with 32-wide blocks (four 48 KB stages), plain ones with 64-wide blocks
-  // (four 48 KB stages as well).  SXL_TC_BK=32 or 64 forces one width.
+// K-block per product form (measured at n = 9216): split products run best
+// with 32-wide blocks (four 48 KB stages), plain ones with 64-wide blocks
+// (four 48 KB stages as well).  SXL_TC_BK=32 or 64 forces one width.
+static int tc_bk(bool split) {
   static const int bk_env = [] {
     const char* e = getenv("SXL_TC_BK");
     return e ? atoi(e) : 0;
   }();
-  const int bk = (bk_env == 32 || bk_env == 64) ? bk_env : (split ? 32 : 64);
+  return (bk_env == 32 || bk_env == 64) ? bk_env : (split ? 32 : 64);
+}
+
+// The product over the k blocks [kb0, kb0 + nkb) of K (nkb = 0: all of K).
+static int gemm_tc_range(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C, float alpha,
+                         const MatH* E, float beta, float gamma, bool sym, bool split, int kb0,
+                         int nkb) {
+  const bool bf16 = c->p.precision == SXL_MIXED_BF16;
+  const int n = c->Np;
+  const int bk = tc_bk(split);
   // plain products cover 256 rows per CTA (two M = 128 MMAs per B tile);
   // SXL_TC_MT=1 restores 128-row tiles
   static const int mt_env = [] {
@@ -566,7 +572,8 @@ int gemm_tc(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C, float alpha
   a.n = n;
   a.ntm = (n + TC_BM * mt - 1) / (TC_BM * mt);
   a.ntn = (n + TC_BN - 1) / TC_BN;
-  a.nk = n / bk;
+  a.nk = nkb > 0 ? nkb : n / bk;
+  a.kb0 = kb0;
   a.nk_half = 0;
   a.alpha = alpha;
   a.beta = beta;
@@ -588,6 +595,39 @@ int gemm_tc(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C, float alpha
   }
   if (bk == 64) return bf16 ? launch_tc<true, false, 64>(c, maps, a) : launch_tc<false, false, 64>(c, maps, a);
   return bf16 ? launch_tc<true, false, 32>(c, maps, a) : launch_tc<false, false, 32>(c, maps, a);
+}
+
+int gemm_tc(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C, float alpha,
+            const MatH* E, float beta, float gamma, bool sym, bool split) {
+  return gemm_tc_range(c, A, B, C, alpha, E, beta, gamma, sym, split, 0, 0);
+}
+
+// The same product with its K sum split into `chunks` launches.  The tensor
+// cores accumulate in fp32 with an error that grows with the number of terms
+// (measured: a mean relative bias of -5.4e-5 over K = 9216 against -6.2e-6 over
+// K = 1152); each launch sums K / chunks terms and the partial results are
+// added in the fp32 epilogue with round-to-nearest, through `tmp` (which must
+// not alias A, B, C or E).
+int gemm_tc_k(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C, float alpha,
+              const MatH* E, float beta, float gamma, bool sym, bool split, int chunks,
+              const MatH& tmp) {
+  const int nkb = c->Np / tc_bk(split);
+  if (chunks > nkb) chunks = nkb;
+  if (chunks <= 1) return gemm_tc(c, A, B, C, alpha, E, beta, gamma, sym, split);
+  const int per = (nkb + chunks - 1) / chunks;
+  chunks = (nkb + per - 1) / per;
+  const MatH* prev = nullptr;
+  for (int j = 0; j < chunks; ++j) {
+    const MatH& out = ((chunks - 1 - j) % 2 == 0) ? C : tmp;  // the last launch writes C
+    const int kb0 = j * per;
+    const int cnt = std::min(per, nkb - kb0);
+    if (j == 0)
+      SXL_TRY(gemm_tc_range(c, A, B, out, alpha, E, beta, gamma, sym, split, kb0, cnt));
+    else
+      SXL_TRY(gemm_tc_range(c, A, B, out, alpha, prev, 1.f, 0.f, sym, split, kb0, cnt));
+    prev = &out;
+  }
+  return SXL_OK;
 }
 
 // C = alpha (A1 B1^T + A2 B2^T) + beta E + gamma I (plain products on the hi
@@ -835,15 +875,27 @@ __global__ void k_rowdot2_h(int np, int n, const uint16_t* ahi, const uint16_t* 
   if (row >= 2 * n) return;
   int b = row / n, i = row % n;
   size_t base = (size_t)b * np * np + (size_t)i * np;
-  double acc = 0.0;
+  // The terms of a diagonal element of dT cancel strongly, so the sum is kept
+  // in double-single form: each product exactly as p + e (p = rn(x y),
+  // e = fma(x, y, -p)), added to (s, c) with Knuth's two-sum; fp32 operations
+  // only, which GB300 runs far faster than fp64 ones.
+  float sh = 0.f, sl = 0.f;
   for (int j = 8 * lane; j < np; j += 256) {
-    // fp64 products: the terms of a diagonal element of dT cancel strongly
     float x[8], y[8];
     ld8<BF16>(ahi, alo, base + j, x);
     ld8<BF16>(bhi, blo, base + j, y);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) acc = fma((double)x[k], (double)y[k], acc);
+    for (int k = 0; k < 8; ++k) {
+      // explicit round-to-nearest operations: no contraction into FMAs
+      const float p = __fmul_rn(x[k], y[k]);
+      const float e = fmaf(x[k], y[k], -p);
+      const float t = __fadd_rn(sh, p);
+      const float z = __fsub_rn(t, sh);
+      sl = __fadd_rn(sl, __fadd_rn(__fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(p, z)), e));
+      sh = t;
+    }
   }
+  double acc = (double)sh + (double)sl;
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if (lane == 0) out[row] = scale * acc;
 }
@@ -900,7 +952,7 @@ int sxl_mixed_supported(sxl_ctx* c) {
     CUDA_TRY(c, cudaMemset(g_tc_err, 0, sizeof(int)));
   }
   MatH* ms[] = {&c->hU, &c->hS, &c->hQ, &c->hX0, &c->hX1, &c->hP, &c->hSm, &c->hdTa, &c->hdTb, &c->hG1,
-                &c->hTeff, &c->hXs};
+                &c->hTeff};
   for (MatH* m : ms) SXL_TRY(halloc(c, m));
   CUDA_TRY(c, cudaMalloc((void**)&c->dup, 2 * (size_t)c->Np * sizeof(double)));
   c->teff_valid = false;
@@ -909,7 +961,7 @@ int sxl_mixed_supported(sxl_ctx* c) {
 
 void sxl_mixed_free(sxl_ctx* c) {
   MatH* ms[] = {&c->hU, &c->hS, &c->hQ, &c->hX0, &c->hX1, &c->hP, &c->hSm, &c->hdTa, &c->hdTb, &c->hG1,
-                &c->hTeff, &c->hXs};
+                &c->hTeff};
   for (MatH* m : ms) hfree(*m);
   if (c->fscratch) cudaFree(c->fscratch);
   c->fscratch = nullptr;
@@ -958,6 +1010,15 @@ int foe_mixed(sxl_ctx* c, double mu, double* stats_dev) {
   const int N = c->N, Np = c->Np, nr = c->nr;
   SXL_TRY(ensure_chain_h(c, nr));
   const bool split = true;
+  // Split products of the density chain sum K in kc launches (gemm_tc_k).
+  // Measured at 1024 atoms against the oracle (fp16): max force error 1.2e-3,
+  // 6.3e-4 and 3.6e-4 eV/A for kc = 1, 2 and 4, density phase 180, 187 and
+  // 210 ms.  SXL_KCHUNK overrides the default of 2.
+  static const int kc = [] {
+    const char* e = getenv("SXL_KCHUNK");
+    return e ? std::max(1, atoi(e)) : 2;
+  }();
+  const MatH& tmp = c->hG1;
   c->umax = c->scale * std::max(std::fabs(c->lam_max - mu), std::fabs(mu - c->lam_min));
   // the start polynomial is monotone with |p(u)| < 1 up to |u| ~ 1.2; the
   // entropy's start correction is fitted on |u| <= 1
@@ -968,22 +1029,21 @@ int foe_mixed(sxl_ctx* c, double mu, double* stats_dev) {
   size_t total = (size_t)Np * Np;
   DISPATCH(c, k_build_u_h, (unsigned)((total + 255) / 256), 256, 0, c->nat, Np, c->H0, c->shift, mu,
            c->scale, c->lam_max, c->hU.hi, c->hU.lo);
-  SXL_TRY(gemm_tc(c, c->hU, c->hU, c->hS, 1.f, nullptr, 0.f, 0.f, true, split));
-  SXL_TRY(gemm_tc(c, c->hS, c->hS, c->hQ, (float)(2.0 / 15.0), &c->hS, (float)(-1.0 / 3.0), 1.f,
-                  true, split));
-  SXL_TRY(gemm_tc(c, c->hU, c->hQ, c->hT[0], 1.f, nullptr, 0.f, 0.f, true, split));
+  SXL_TRY(gemm_tc_k(c, c->hU, c->hU, c->hS, 1.f, nullptr, 0.f, 0.f, true, split, kc, tmp));
+  SXL_TRY(gemm_tc_k(c, c->hS, c->hS, c->hQ, (float)(2.0 / 15.0), &c->hS, (float)(-1.0 / 3.0), 1.f,
+                    true, split, kc, tmp));
+  SXL_TRY(gemm_tc_k(c, c->hU, c->hQ, c->hT[0], 1.f, nullptr, 0.f, 0.f, true, split, kc, tmp));
   double t = std::min(tanh5(c->umax), 1.0);
   // the split products carry about 22 bits (fp16) or 16 bits (bf16): a
   // Newton-Schulz error bound of 1e-7 is at that floor
   const double tol = 1e-7;
   c->teff_valid = false;
-  c->shift_tau = 0.0;
   c->fo_h = 0.0;
   c->apm_ready = false;
   c->ns_iters.assign(nr, 0);
   for (int k = 0; k < nr; ++k) {
     const MatH& Sq = c->hSm;
-    SXL_TRY(gemm_tc(c, c->hT[k], c->hT[k], Sq, 1.f, nullptr, 0.f, 0.f, true, split));
+    SXL_TRY(gemm_tc_k(c, c->hT[k], c->hT[k], Sq, 1.f, nullptr, 0.f, 0.f, true, split, kc, tmp));
     double s = t * t;
     double ci = 2.0 / (2.0 + s);
     double e = s / (2.0 + s);
@@ -1004,12 +1064,13 @@ int foe_mixed(sxl_ctx* c, double mu, double* stats_dev) {
         // last iteration as a refinement X' = X + R X: the residual
         // R = I - X (I + T^2) needs the split products; R is small, so R X
         // runs on the hi parts (its error is 2^-11 |R|)
-        SXL_TRY(gemm_tc(c, *cur, Sq, c->hP, -1.f, cur, -1.f, 1.f, false, true));
+        SXL_TRY(gemm_tc_k(c, *cur, Sq, c->hP, -1.f, cur, -1.f, 1.f, false, true, kc, tmp));
         SXL_TRY(gemm_tc(c, c->hP, *cur, *nxt, 1.f, cur, 1.f, 0.f, true, false));
       }
       cur = nxt;
     }
-    SXL_TRY(gemm_tc(c, c->hT[k], c->hY[k], c->hT[k + 1], 2.f, nullptr, 0.f, 0.f, true, split));
+    SXL_TRY(gemm_tc_k(c, c->hT[k], c->hY[k], c->hT[k + 1], 2.f, nullptr, 0.f, 0.f, true, split, kc,
+                      tmp));
     t = 2.0 * t / (1.0 + t * t);
   }
   int wpb = 8, rows = 2 * N;
@@ -1021,49 +1082,6 @@ int foe_mixed(sxl_ctx* c, double mu, double* stats_dev) {
 
 const MatH& final_T_mixed(const sxl_ctx* c) { return c->teff_valid ? c->hTeff : c->hT[c->nr]; }
 
-// Exact shift of the chemical potential by dmu: with y = beta (eps - mu)/2
-// and s = beta dmu / 2, tanh(y - s) = (t - tau) / (1 - t tau), tau = tanh(s),
-// so T' = (T - tau I)(I - tau T)^{-1}.  The inverse comes from Newton-Schulz
-// started at I + tau T (error tau^2 T^2); tau is small in MD, so two or three
-// iterations suffice.  The result replaces the final T (hTeff); the response
-// chain keeps T_nr.  c->shift_tau records tau for the entropy.
-int mu_shift_exact_mixed(sxl_ctx* c, double dmu, double* stats_dev) {
-  const int N = c->N;
-  const MatH& T = c->hT[c->nr];
-  const double tau = std::tanh(0.5 * c->beta * dmu);
-  // M = I - tau T (in hSm), X = I + tau T
-  axpy_diag_h(c, c->hSm, -tau, T, 1.0);
-  axpy_diag_h(c, c->hX0, tau, T, 1.0);
-  const MatH* cur = &c->hX0;
-  double e = tau * tau;
-  int it = 0;
-  while (e > 1e-7 && it < 6) {
-    const MatH* nxt = (cur == &c->hX0) ? &c->hX1 : &c->hX0;
-    if (e > 1e-3) {
-      SXL_TRY(gemm_tc(c, *cur, c->hSm, c->hP, 1.f, nullptr, 0.f, 0.f, false, false));
-      SXL_TRY(gemm_tc(c, c->hP, *cur, *nxt, -1.f, cur, 2.f, 0.f, true, false));
-    } else {
-      SXL_TRY(gemm_tc(c, *cur, c->hSm, c->hP, -1.f, nullptr, 0.f, 1.f, false, true));
-      SXL_TRY(gemm_tc(c, c->hP, *cur, *nxt, 1.f, cur, 1.f, 0.f, true, false));
-    }
-    cur = nxt;
-    e = std::max(e * e, 1e-14);
-    ++it;
-  }
-  // T' = T X - tau X (T and X commute: a symmetric product)
-  SXL_TRY(gemm_tc(c, T, *cur, c->hTeff, 1.f, cur, (float)(-tau), 0.f, true, true));
-  // keep X = (I - tau T)^{-1}: the response maps dT to dT' = (1 - tau^2) X dT X
-  std::swap(c->hXs, cur == &c->hX0 ? c->hX0 : c->hX1);
-  c->teff_valid = true;
-  c->shift_tau = tau;
-  c->fo_h = 0.0;
-  int wpb = 8, rows = 2 * N;
-  DISPATCH(c, k_rowstats_h, (rows + wpb - 1) / wpb, 32 * wpb, 0, c->Np, N, c->hTeff.hi,
-           c->hTeff.lo, c->diagT, c->rowsq);
-  small_kernels_density(c, c->q, stats_dev);
-  return SXL_OK;
-}
-
 // First-order shift of the chemical potential by dmu without rerunning the
 // expansion: dD/dmu = beta D (I - D) = beta (I - T^2) / 4 exactly (the
 // perturbation commutes with H), so T_eff = T - (beta dmu / 2)(I - T^2)
@@ -1072,14 +1090,8 @@ int mu_shift_exact_mixed(sxl_ctx* c, double dmu, double* stats_dev) {
 int mu_shift_mixed(sxl_ctx* c, double dmu, double* stats_dev) {
   const int N = c->N;
   const float h = (float)(0.5 * c->beta * dmu);
-  if (c->teff_valid) {
-    // on top of an exact shift: T_eff2 from T_eff, via hSm, then swap
-    SXL_TRY(gemm_tc(c, c->hTeff, c->hTeff, c->hSm, h, &c->hTeff, 1.f, -h, true, true));
-    std::swap(c->hSm, c->hTeff);
-  } else {
-    const MatH& T = c->hT[c->nr];
-    SXL_TRY(gemm_tc(c, T, T, c->hTeff, h, &T, 1.f, -h, true, true));
-  }
+  const MatH& T = c->hT[c->nr];
+  SXL_TRY(gemm_tc(c, T, T, c->hTeff, h, &T, 1.f, -h, true, true));
   c->teff_valid = true;
   c->fo_h = 0.5 * c->beta * dmu;
   int wpb = 8, rows = 2 * N;
@@ -1119,7 +1131,6 @@ int dmpt_mixed(sxl_ctx* c, const double* du_real) {
   //   dT_{k+1} = A- dT A+ + A+ dT A- = A- V^T + V A-,  V = A+ dT.
   // One full product and one symmetric product over [A- | V][V | A-]^T per
   // step (the three-product form needs half a product more).
-  const bool shifted = c->teff_valid && c->shift_tau != 0.0;
   if (!c->apm_ready) {
     const size_t pairs = (size_t)Np * Np;
     for (int k = 0; k < nr; ++k)
@@ -1127,36 +1138,24 @@ int dmpt_mixed(sxl_ctx* c, const double* du_real) {
                c->hY[k].lo, c->hT[k + 1].hi, c->hT[k + 1].lo, c->hAm[k].hi, c->hAm[k].lo);
     // A first-order shift T_eff = T + h (T^2 - I) after the chain maps
     // dT -> dT + h (T dT + dT T) = (I + h T) dT (I + h T) + O(h^2): it folds
-    // into the last operators, A+- -> (I + h T_nr) A+-, or, after an exact
-    // shift, X -> (I + h T') X (T' ~ T_eff to O(h)).  Products of commuting
-    // matrices: symmetric outputs.
+    // into the last operators, A+- -> (I + h T_nr) A+- (products of commuting
+    // matrices: symmetric outputs).
     if (c->fo_h != 0.0) {
       const float h = (float)c->fo_h;
-      if (!shifted) {
-        MatH& Ap = c->hY[nr - 1];
-        MatH& Am = c->hAm[nr - 1];
-        SXL_TRY(gemm_tc(c, c->hT[nr], Ap, c->hX0, h, &Ap, 1.f, 0.f, true, false));
-        SXL_TRY(gemm_tc(c, c->hT[nr], Am, c->hX1, h, &Am, 1.f, 0.f, true, false));
-        std::swap(Ap, c->hX0);
-        std::swap(Am, c->hX1);
-      } else {
-        SXL_TRY(gemm_tc(c, c->hTeff, c->hXs, c->hX0, h, &c->hXs, 1.f, 0.f, true, true));
-        std::swap(c->hXs, c->hX0);
-      }
+      MatH& Ap = c->hY[nr - 1];
+      MatH& Am = c->hAm[nr - 1];
+      SXL_TRY(gemm_tc(c, c->hT[nr], Ap, c->hX0, h, &Ap, 1.f, 0.f, true, false));
+      SXL_TRY(gemm_tc(c, c->hT[nr], Am, c->hX1, h, &Am, 1.f, 0.f, true, false));
+      std::swap(Ap, c->hX0);
+      std::swap(Am, c->hX1);
     }
     c->apm_ready = true;
   }
   // Only diag(dT_nr) is needed (q_v): the last step ends in row dots,
-  // diag(A- V^T + V A-) = 2 rowdot(A-, V), and with an exact shift the map
-  // (1 - tau^2) X dT X ends in diag(X dT X) = rowdot(X dT, X).
+  // diag(A- V^T + V A-) = 2 rowdot(A-, V).
   const int wpb = 8;
-  for (int k = 0; k < nr; ++k) {
+  for (int k = 0; k < nr - 1; ++k) {
     SXL_TRY(gemm_tc(c, c->hY[k], *dA, c->hG1, 1.f, nullptr, 0.f, 0.f, false, split));
-    if (k == nr - 1 && !shifted) {
-      DISPATCH(c, k_rowdot2_h, (2 * N + wpb - 1) / wpb, 32 * wpb, 0, Np, N, c->hAm[k].hi,
-               c->hAm[k].lo, c->hG1.hi, c->hG1.lo, 2.0, c->diagT + 2 * N);
-      return SXL_OK;
-    }
     if (split) {
       SXL_TRY(gemm_tc(c, c->hAm[k], c->hG1, c->hP, 1.f, nullptr, 0.f, 0.f, false, split));
       symcombo_h(c, *dB, 0.0, nullptr, 1.0, &c->hP, 0.0, nullptr, nullptr);
@@ -1166,12 +1165,9 @@ int dmpt_mixed(sxl_ctx* c, const double* du_real) {
     }
     std::swap(dA, dB);
   }
-  // the final T was shifted exactly (tanh addition): the same map carries
-  // the response, dT' = (1 - tau^2) X dT X with X = (I - tau T)^{-1}.  X has
-  // entries up to 1 / (1 - |tau|), so this one product runs in split form.
-  SXL_TRY(gemm_tc(c, c->hXs, *dA, c->hG1, 1.f, nullptr, 0.f, 0.f, false, true));
-  DISPATCH(c, k_rowdot2_h, (2 * N + wpb - 1) / wpb, 32 * wpb, 0, Np, N, c->hG1.hi, c->hG1.lo,
-           c->hXs.hi, c->hXs.lo, 1.0 - c->shift_tau * c->shift_tau, c->diagT + 2 * N);
+  SXL_TRY(gemm_tc(c, c->hY[nr - 1], *dA, c->hG1, 1.f, nullptr, 0.f, 0.f, false, split));
+  DISPATCH(c, k_rowdot2_h, (2 * N + wpb - 1) / wpb, 32 * wpb, 0, Np, N, c->hAm[nr - 1].hi,
+           c->hAm[nr - 1].lo, c->hG1.hi, c->hG1.lo, 2.0, c->diagT + 2 * N);
   return SXL_OK;
 }
 
@@ -1382,44 +1378,19 @@ __global__ void k_dot_hl_partial(long long len, const uint16_t* ah, const uint16
   }
   if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
 }
-// sum_a s(f_a) = -N ln 2 - Tr ln cosh(Y') + Tr(Y' T') per spin, with
-// Y' = Y - sh I after an exact shift (sh = beta dmu / 2, 0 without one):
-// Tr ln cosh(Y') = Tr ln cosh(Y) + N ln cosh(sh) + ln det(I - tanh(sh) T),
-// Tr(Y' T') = 2^nr <U, T'> - sh Tr T'.
+// sum_a s(f_a) = -N ln 2 - Tr ln cosh(Y) + Tr(Y T) per spin, from the
+// log-determinants of the chain (ld) and Tr(Y T) = 2^nr (<U, T> + <delta(U), T>)
 __global__ void k_entropy_combine(int N, int nr, const double* ld, const double* dots, double* out,
-                                  double sh, const double* ldsh, const double* trT,
                                   const double* corr, double wcorr) {
   if (threadIdx.x != 0) return;
   double tot = 0.0;
-  const double lch = sh != 0.0 ? log(cosh(sh)) : 0.0;
   for (int s = 0; s < 2; ++s) {
     double v = -N * 0.69314718055994531 + ldexp(1.0, nr - 1) * ld[s] +
                ldexp(1.0, nr) * (dots[s] + wcorr * corr[s]);
     for (int k = 0; k < nr; ++k) v += ldexp(1.0, nr - 1 - k) * ld[2 * (k + 1) + s];
-    v -= N * lch + ldsh[s];
-    v -= sh * trT[s];
     tot += v;
   }
   out[0] = tot;
-}
-
-// trT[s] = Tr T_s (both spins), fp64 sums
-template <bool BF16>
-__global__ void k_trace2_h(int n, const uint16_t* hi, const uint16_t* lo, double* trT) {
-  __shared__ double sm[1024];
-  for (int s = 0; s < 2; ++s) {
-    double a = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-      a += ld_hl_d<BF16>(hi, lo, (size_t)s * n * n + (size_t)i * n + i);
-    sm[threadIdx.x] = a;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) trT[s] = sm[0];
-    __syncthreads();
-  }
 }
 
 int entropy_mixed(sxl_ctx* c, double* out_dev) {
@@ -1449,17 +1420,10 @@ int entropy_mixed(sxl_ctx* c, double* out_dev) {
     chol_logdet_dev_f32(c, N, c->fscratch, ld + 2 * (k + 1));
   }
   LAUNCH(k_negate_pairs, 1, 64, 0, c->st, nr, ld);
-  // exact chemical-potential shift: ln cosh(y - s) = ln cosh y + ln cosh s + ln(1 - t tau)
-  double* ldsh = c->red + 3180;  // 2: ln det(I - tau T) per spin
-  double* trT = c->red + 3184;   // 2: Tr T' per spin
-  CUDA_TRY(c, cudaMemsetAsync(ldsh, 0, 2 * sizeof(double), c->st));
-  if (c->teff_valid && c->shift_tau != 0.0) {
-    DISPATCH(c, k_hl_to_f32, g, 256, 0, nn2, c->hT[nr].hi, c->hT[nr].lo, c->fscratch,
-             (float)c->shift_tau);
-    chol_logdet_dev_f32(c, N, c->fscratch, ldsh);
-  }
+  // A first-order shift of mu on top of the chain (T_eff) changes
+  // -Tr ln cosh Y + Tr(Y T) only at second order in the shift: the shifted
+  // argument's two first-order terms, -s Tr T from each, cancel.
   const MatH& Tf = final_T_mixed(c);
-  DISPATCH(c, k_trace2_h, 1, 1024, 0, N, Tf.hi, Tf.lo, trT);
   for (int s = 0; s < 2; ++s) {
     DISPATCH(c, k_dot_hl_partial, 128, 256, 0, (long long)nn, c->hU.hi + s * nn, c->hU.lo + s * nn,
              Tf.hi + s * nn, Tf.lo + s * nn, c->red + 2048);
@@ -1495,7 +1459,6 @@ int entropy_mixed(sxl_ctx* c, double* out_dev) {
       LAUNCH(k_sum_parts, 1, 256, 0, c->st, 128, c->red + 2048, corr + s);
     }
   }
-  const double sh = c->teff_valid ? std::atanh(c->shift_tau) : 0.0;
-  LAUNCH(k_entropy_combine, 1, 32, 0, c->st, N, nr, ld, dots, out_dev, sh, ldsh, trT, corr, wcorr);
+  LAUNCH(k_entropy_combine, 1, 32, 0, c->st, N, nr, ld, dots, out_dev, corr, wcorr);
   return SXL_OK;
 }
