@@ -1118,8 +1118,15 @@ int dmpt_mixed(sxl_ctx* c, const double* du_real) {
   LAUNCH(k_pad_vec, (2 * Np + 255) / 256, 256, 0, c->st, N, Np, du_real, du);
   const MatH& dS = c->hSm;
   symcombo_h(c, dS, 0.0, nullptr, 0.0, nullptr, 1.0, du, &c->hU);
-  SXL_TRY(gemm_tc(c, dS, c->hS, c->hG1, 1.f, nullptr, 0.f, 0.f, false, split));
-  symcombo_h(c, c->hP, -1.0 / 3.0, &dS, 2.0 / 15.0, &c->hG1, 0.0, nullptr, nullptr);
+  // P = dQ = -dS/3 + (2/15)(dS S + S dS): in the plain form one symmetric
+  // product over [dS | S][S | dS]^T with the -dS/3 term in its epilogue
+  if (split) {
+    SXL_TRY(gemm_tc(c, dS, c->hS, c->hG1, 1.f, nullptr, 0.f, 0.f, false, split));
+    symcombo_h(c, c->hP, -1.0 / 3.0, &dS, 2.0 / 15.0, &c->hG1, 0.0, nullptr, nullptr);
+  } else {
+    SXL_TRY(gemm_tc_dual(c, dS, c->hS, c->hS, dS, c->hP, (float)(2.0 / 15.0), &dS,
+                         (float)(-1.0 / 3.0), 0.f, true));
+  }
   SXL_TRY(gemm_tc(c, c->hU, c->hP, c->hG1, 1.f, nullptr, 0.f, 0.f, false, split));
   const MatH* dA = &c->hdTa;
   const MatH* dB = &c->hdTb;
