@@ -265,18 +265,38 @@ static int density(sxl_ctx* c, const double* R, const double* n, double mu_guess
     if (it + 1 >= maxit)
       return sxl_fail(c, SXL_E_NO_CONVERGENCE, "chemical potential search hit its iteration cap");
     if (err > 0) hi = mu; else lo = mu;
-    // mixed forms: a remaining Newton step with beta |dmu| <= 1e-2 is
-    // applied to the final T to first order (neglected term <= (beta dmu)^2
-    // / 20) instead of another pass; the response follows it.
-    if (mixed && dN > 0 && c->beta * std::fabs(err / dN) <= 1e-2) {
-      const double dmu = -err / dN;
-      SXL_TRY(mu_shift_mixed(c, dmu, stats));
-      SXL_TRY(sync_host(c, stats, 2));
-      mu += dmu;
-      c->last_N = c->hred[0];
-      if (dbg)
-        fprintf(stderr, "[sxl] mu first-order shift %.3e -> N %.10f\n", dmu, c->hred[0]);
-      break;
+    // mixed forms: a remaining Newton step with beta |dmu| <= 0.1 is applied
+    // to the final T to second order (neglected term <= (beta dmu / 2)^3 / 3)
+    // instead of another pass.  The shift is repeated from T_nr with the
+    // accumulated dmu until |N - N_e| < tol (a Newton step in mu leaves
+    // N'' dmu^2 / 2); if that does not settle, a full pass runs at the shifted
+    // mu.  The response follows the shift to first order.
+    if (mixed && dN > 0 && c->beta * std::fabs(err / dN) <= 0.1) {
+      double total = 0.0, step = -err / dN;
+      bool settled = false;
+      for (int e = 0; e < 4; ++e) {
+        if (c->beta * std::fabs(total + step) > 0.1) break;
+        total += step;
+        SXL_TRY(mu_shift_mixed(c, total, stats));
+        SXL_TRY(sync_host(c, stats, 2));
+        const double err2 = c->hred[0] - Ne;
+        if (dbg)
+          fprintf(stderr, "[sxl] mu shift %.3e -> N %.10f\n", total, c->hred[0]);
+        if (std::fabs(err2) < tol) {
+          settled = true;
+          break;
+        }
+        step = (c->hred[1] > 0) ? -err2 / c->hred[1] : 0.0;
+      }
+      if (settled) {
+        mu += total;
+        c->last_N = c->hred[0];
+        break;
+      }
+      if (it + 1 >= maxit)
+        return sxl_fail(c, SXL_E_NO_CONVERGENCE, "chemical potential search hit its iteration cap");
+      mu += (total != 0.0) ? total : step;
+      continue;
     }
     double mn = (dN > 0) ? mu - err / dN : 0.5 * (lo + hi);
     if (!(mn > lo && mn < hi)) mn = 0.5 * (lo + hi);
