@@ -76,7 +76,7 @@ struct sxl_ctx {
   MatH hTeff;             // T_nr after a first-order chemical-potential shift
   float* fscratch;        // 2 Np^2 fp32 (entropy factorizations, mixed forms)
   bool teff_valid;        // hTeff (not hT[nr]) holds the final density
-  double fo_h;            // h = beta dmu / 2 of the first-order shift in hTeff (0: none)
+  double fo_h;            // h = beta dmu / 2 of the mu shift in hTeff (0: none)
   double mu_prev;         // chemical potential of the previous MD step (NaN: none)
   // DIIS history (scf.cu): rings of DIIS_MAX input / residual vectors
   double *diis_N, *diis_F, *diis_B, *diis_coef;

@@ -1149,10 +1149,10 @@ int dmpt_mixed(sxl_ctx* c, const double* du_real) {
     for (int k = 0; k < nr; ++k)
       DISPATCH(c, k_apm_h, (unsigned)((pairs + 255) / 256), 256, 0, pairs, c->hY[k].hi,
                c->hY[k].lo, c->hT[k + 1].hi, c->hT[k + 1].lo, c->hAm[k].hi, c->hAm[k].lo);
-    // A first-order shift T_eff = T + h (T^2 - I) after the chain maps
-    // dT -> dT + h (T dT + dT T) = (I + h T) dT (I + h T) + O(h^2): it folds
-    // into the last operators, A+- -> (I + h T_nr) A+- (products of commuting
-    // matrices: symmetric outputs).
+    // The mu shift after the chain, T_eff = T + h (T^2 - I) + O(h^2), maps
+    // dT -> dT + h (T dT + dT T) = (I + h T) dT (I + h T) + O(h^2): to first
+    // order it folds into the last operators, A+- -> (I + h T_nr) A+-
+    // (products of commuting matrices: symmetric outputs).
     if (c->fo_h != 0.0) {
       const float h = (float)c->fo_h;
       MatH& Ap = c->hY[nr - 1];
@@ -1363,8 +1363,8 @@ extern "C" int sxl_mixed_gemm_noalloc(int n, int precision, const double* A, con
 
 // ---------------------------------------------------------------------------
 // entropy (see chol.cu): out[0] = sum_spins sum_a [f ln f + (1 - f) ln(1 - f)]
-// from the chain of the last expansion pass (its chemical potential; a
-// first-order shift applied afterwards is not carried into this term).
+// from the chain of the last expansion pass, with Tr(Y T) taken on the final
+// (shifted) T; the shift's effect on the rest enters at second order.
 template <bool BF16>
 __global__ void k_hl_to_f32(size_t nn, const uint16_t* hi, const uint16_t* lo, float* out,
                             float scale) {
@@ -1433,9 +1433,9 @@ int entropy_mixed(sxl_ctx* c, double* out_dev) {
     chol_logdet_dev_f32(c, N, c->fscratch, ld + 2 * (k + 1));
   }
   LAUNCH(k_negate_pairs, 1, 64, 0, c->st, nr, ld);
-  // A first-order shift of mu on top of the chain (T_eff) changes
-  // -Tr ln cosh Y + Tr(Y T) only at second order in the shift: the shifted
-  // argument's two first-order terms, -s Tr T from each, cancel.
+  // A shift of mu on top of the chain (T_eff) changes -Tr ln cosh Y + Tr(Y T)
+  // only at second order in the shift: the shifted argument's two
+  // first-order terms, -s Tr T from each, cancel.
   const MatH& Tf = final_T_mixed(c);
   for (int s = 0; s < 2; ++s) {
     DISPATCH(c, k_dot_hl_partial, 128, 256, 0, (long long)nn, c->hU.hi + s * nn, c->hU.lo + s * nn,
