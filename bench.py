@@ -120,19 +120,29 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def kernel_source_hash(path: str) -> str:
+    """Hash of a CUDA source with comments and whitespace removed, so that only
+    code changes invalidate counters taken on it."""
+    import hashlib
+    import re
+    src = open(path).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    src = re.sub(r"\s+", "", src)
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
+
+
 def traffic_record():
     """ncu DRAM traffic of the tensor-core GEMM per launch, if a capture of the
-    current kernel source exists (profiles/tc_gemm_traffic.json holds the
-    source hash it was taken on)."""
-    import hashlib
+    current kernel code exists (profiles/tc_gemm_traffic.json holds the code
+    hash it was taken on)."""
     path = os.path.join(ROOT, "profiles", "tc_gemm_traffic.json")
     src = os.path.join(ROOT, "paper_2303_03529_gb300", "csrc", "mixed.cu")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         rec = json.load(f)
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if rec.get("source_sha") != h:
+    if rec.get("source_sha") != kernel_source_hash(src):
         return None
     return rec
 
