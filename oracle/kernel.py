@@ -19,6 +19,54 @@ from __future__ import annotations
 import numpy as np
 
 
+class KrylovBuilder:
+    """The Krylov loop of Eq. mIJacobian one direction at a time, so that a
+    caller can time or inspect every direction (each needs one response).
+
+    add_direction() orthogonalizes the current candidate against the previous
+    v's (two passes of modified Gram-Schmidt), normalizes it, takes its
+    response f~_v = K0 (q_v - v) and solves min |F~ c - f~|; it returns False
+    at breakdown (the candidate is numerically inside the span)."""
+
+    def __init__(self, dens, K0, f=None, breakdown=1e-12):
+        self.dens, self.K0, self.breakdown = dens, K0, breakdown
+        self.f = dens.residual() if f is None else f
+        self.ft = K0 @ self.f
+        self.nft = np.linalg.norm(self.ft)
+        self.V, self.FT = [], []
+        self.c = np.zeros(0)
+        self.rel = 1.0
+        self.w = self.ft.copy()
+
+    def add_direction(self):
+        w = self.w
+        for _ in range(2):
+            for v in self.V:
+                w = w - (v @ w) * v
+        nw = np.linalg.norm(w)
+        if nw <= self.breakdown * max(self.nft, 1e-300):
+            return False
+        v = w / nw
+        fv = self.dens.fv(v)
+        self.V.append(v)
+        self.FT.append(self.K0 @ fv)
+        Fm = np.array(self.FT).T
+        self.c = np.linalg.lstsq(Fm, self.ft, rcond=None)[0]
+        self.rel = np.linalg.norm(Fm @ self.c - self.ft) / max(self.nft, 1e-300)
+        self.w = self.FT[-1].copy()
+        return True
+
+    def result(self):
+        """(K f ~ V c, info) for the directions added so far."""
+        f = self.f
+        if not self.V:
+            return np.zeros_like(f), dict(V=np.zeros((f.size, 0)), FT=np.zeros((f.size, 0)),
+                                          c=self.c, rel=self.rel, rank=0)
+        Vm = np.array(self.V).T
+        return Vm @ self.c, dict(V=Vm, FT=np.array(self.FT).T, c=self.c, rel=self.rel,
+                                 rank=len(self.V))
+
+
 def krylov_kernel(dens, K0, rank, f=None, rel_tol=None, breakdown=1e-12):
     """Low-rank K f for the density `dens` (an electronic.Density).
 
@@ -27,36 +75,13 @@ def krylov_kernel(dens, K0, rank, f=None, rel_tol=None, breakdown=1e-12):
               |F~ c - f~| / |f~| < rel_tol (the SCF's "2-3 ranks adaptively").
     Returns (Kf, info) with info holding V, F~, c and the relative LSQ
     residual."""
-    if f is None:
-        f = dens.residual()
-    ft = K0 @ f
-    nft = np.linalg.norm(ft)
-    V, FT = [], []
-    c = np.zeros(0)
-    rel = 1.0
-    w = ft.copy()
-    for k in range(rank):
-        for _ in range(2):
-            for v in V:
-                w = w - (v @ w) * v
-        nw = np.linalg.norm(w)
-        if nw <= breakdown * max(nft, 1e-300):
+    kb = KrylovBuilder(dens, K0, f=f, breakdown=breakdown)
+    for _ in range(rank):
+        if not kb.add_direction():
             break
-        v = w / nw
-        fv = dens.fv(v)
-        V.append(v)
-        FT.append(K0 @ fv)
-        Fm = np.array(FT).T
-        c = np.linalg.lstsq(Fm, ft, rcond=None)[0]
-        rel = np.linalg.norm(Fm @ c - ft) / max(nft, 1e-300)
-        if rel_tol is not None and rel < rel_tol:
+        if rel_tol is not None and kb.rel < rel_tol:
             break
-        w = FT[-1].copy()
-    if not V:
-        return np.zeros_like(f), dict(V=np.zeros((f.size, 0)), FT=np.zeros((f.size, 0)),
-                                      c=c, rel=rel, rank=0)
-    Vm = np.array(V).T
-    return Vm @ c, dict(V=Vm, FT=np.array(FT).T, c=c, rel=rel, rank=len(V))
+    return kb.result()
 
 
 def exact_kernel(dens):

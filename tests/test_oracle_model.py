@@ -139,3 +139,96 @@ def test_gamma_matrix():
     R = np.array([[0.0, 0, 0], [40.0, 0, 0]])
     G2 = model.gamma_matrix(R, np.array([200.0, 200, 200]), P)
     assert abs(G2[0, 1] - P.coulomb_k / 40.0) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Radial law of the bond integrals.  The workload's model fixes every bond
+# integral as V(r) = V0 exp(-1.5/A (r - 2.48 A)) with the V0 table
+# ssS -1.5, spS 1.8, sdS -1.0, ppS 2.5, ppP -0.6, pdS -1.2, pdP 0.5,
+# ddS -0.9, ddP 0.5, ddD -0.08 eV and a smooth cutoff at 5 A.  The numbers
+# below are typed from that statement, not read from the parameter object,
+# so a wrong exponent sign, decay, reference length or table entry fails.
+V0_TABLE = (-1.5, 1.8, -1.0, 2.5, -0.6, -1.2, 0.5, -0.9, 0.5, -0.08)
+
+
+def test_bond_integrals_equal_table_at_reference_length():
+    V = model.bond_integrals(2.48, P)
+    assert tuple(V) == V0_TABLE
+
+
+@pytest.mark.parametrize("r", [2.2, 3.0, 4.0, 4.4])
+def test_bond_integrals_radial_decay(r):
+    V = np.array(model.bond_integrals(r, P))
+    expect = np.array(V0_TABLE) * np.exp(-1.5 * (r - 2.48))
+    np.testing.assert_allclose(V, expect, rtol=1e-14)
+
+
+def test_bond_integrals_vanish_beyond_cutoff():
+    for r in (5.0, 5.2, 7.0):
+        assert all(v == 0.0 for v in model.bond_integrals(r, P))
+    # inside the switch the integrals are damped but keep their sign
+    V = np.array(model.bond_integrals(4.75, P))
+    undamped = np.array(V0_TABLE) * np.exp(-1.5 * (4.75 - 2.48))
+    ratio = V / undamped
+    assert np.all(ratio > 0.0) and np.all(ratio < 1.0)
+    np.testing.assert_allclose(ratio, ratio[0], rtol=1e-14)
+
+
+def test_dimer_hopping_on_z_axis_uses_table_values():
+    """Two atoms 2.48 A apart on z in a large box: the sigma couplings of the
+    Hamiltonian are the table values themselves (s-s, s-pz, pz-pz, s-d3z2,
+    pz-d3z2, d3z2-d3z2) and the pi/delta ones sit on their orbital pairs."""
+    R = np.array([[5.0, 5.0, 5.0], [5.0, 5.0, 7.48]])
+    H = model.build_h0(R, np.array([40.0, 40.0, 40.0]), P)
+    B = H[:9, 9:]
+    s, x, y, z, xy, yz, zx, x2, z2 = range(9)
+    got = [B[s, s], B[s, z], B[s, z2], B[z, z], B[x, x], B[z, z2], B[x, zx], B[z2, z2],
+           B[yz, yz], B[xy, xy]]
+    # 7.48 - 5.0 differs from 2.48 in the last bit, hence rtol 1e-14
+    np.testing.assert_allclose(got, V0_TABLE, rtol=1e-14)
+    assert B[y, y] == B[x, x]
+
+
+# ---------------------------------------------------------------------------
+# Direction of the spin shift.  Without hopping (all V0 = 0) every level is
+# atomic: eps_orbital + (gamma n)_I + sigma (W/2) s_I.  The model states the
+# shift as +-W m_I / 2 with W = -0.6 eV, i.e. the up channel moves by +W/2 per
+# unit spin and, W being negative, down: a positive spin lowers the up levels
+# (Stoner exchange favours magnetization).  Both tests below fail if the sign
+# of the spin term is flipped consistently in H and E.
+def _atomic_pair():
+    p0 = P.replace(V0=(0.0,) * 10)
+    R = np.array([[1.0, 1.0, 1.0], [9.0, 8.0, 7.0]])
+    cell = np.array([40.0, 40.0, 40.0])
+    return p0, model.build_h0(R, cell, p0), model.gamma_matrix(R, cell, p0)
+
+
+def test_spin_shift_splits_atomic_levels_by_w_times_spin():
+    p0, H0, G = _atomic_pair()
+    n = np.array([0.7, 0.1, 0.2, 0.3])          # n_up = (0.7, 0.1), n_dn = (0.2, 0.3)
+    Hu, Hd = model.hamiltonians(H0, n, G, p0)
+    s = np.array([0.5, -0.2])
+    split = np.diag(Hu) - np.diag(Hd)
+    np.testing.assert_allclose(split, np.repeat(-0.6 * s, 9), atol=1e-15)
+    # off-diagonals stay zero and the spin average is the Coulomb shift
+    mean = 0.5 * (np.diag(Hu) + np.diag(Hd)) - np.diag(H0)
+    np.testing.assert_allclose(mean, np.repeat(G @ np.array([0.9, 0.4]), 9), atol=1e-14)
+    assert np.allclose(Hu - np.diag(np.diag(Hu)), 0.0)
+
+
+def test_spin_response_is_ferromagnetic_in_closed_form():
+    """n = 0, no hopping: per spin and atom the five d levels at -6 eV hold
+    4 electrons (s at -3 and p at +3 eV lie above mu and are empty up to
+    e^-28), so f_d = 0.8 and mu = -6 + kT ln 4.  A spin direction v = delta
+    (e_up,0 - e_dn,0) shifts atom 0's levels by +-W delta (its charge part
+    cancels), the common dmu is 0 by symmetry, and each channel's charge
+    moves by -/+ W delta beta 5 f_d (1 - f_d) = +-4.8 delta: the spin grows
+    (q_v,up > 0) because W < 0."""
+    p0, H0, G = _atomic_pair()
+    from oracle import electronic
+    d = electronic.Density(H0, G, np.zeros(4), p0)
+    assert abs(d.mu - (-6.0 + 0.1 * np.log(4.0))) < 1e-12
+    delta = 0.01
+    qv, dmu = d.response(np.array([delta, 0.0, -delta, 0.0]))
+    assert abs(dmu) < 1e-14
+    np.testing.assert_allclose(qv, [4.8 * delta, 0.0, -4.8 * delta, 0.0], atol=1e-12)
