@@ -245,8 +245,10 @@ int sxl_batch_destroy(sxl_batch* batch);
  * N x N, row-major fp64 device arrays, E may be NULL) through the library's
  * tensor-core GEMM, the product every step of the mixed-precision chains
  * uses: inputs are rounded to (hi, lo) 16-bit pairs, split = 1 forms the
- * three-product form, split = 0 the hi x hi product only; sym = 1 computes
- * the upper tiles and mirrors them (valid only for a symmetric result).
+ * three-product form, split = 0 the hi x hi product only, split = 2 the
+ * dual form of the response steps, C = alpha (A B^T + B A^T) + beta E +
+ * gamma I on the hi parts; sym = 1 computes the upper tiles and mirrors
+ * them (valid only for a symmetric result).
  * Needs a context created with SXL_MIXED_FP16 or SXL_MIXED_BF16.  Runs in the
  * context's chain buffers: any density held by the context is discarded
  * (call sxl_density again before sxl_response or sxl_forces). */
@@ -285,6 +287,16 @@ int sxl_mixed_gemm_noalloc(int n, int precision, const double* A_dev, const doub
  * reset = 1 clears the counters after reading. */
 int sxl_timers(sxl_ctx* ctx, double* out10, int reset);
 int sxl_enable_gemm_timing(sxl_ctx* ctx, int on);
+
+/* The same GEMM timing per product form: out16[4 v + j] for v = 0 plain
+ * tensor-core products (one hi x hi MMA per k step), 1 dual products
+ * (A1 B1^T + A2 B2^T over the concatenated K), 2 split products (three MMAs
+ * per k step: hi hi, hi lo, lo hi), 3 fp64 products of the SXL_FP64 form;
+ * j = 0 launches, 1 total ms, 2 flops of the MMAs (or FMA tiles) issued,
+ * 3 flops of the products themselves (2 K per owned output element, each
+ * product counted once whatever its form).  Counts only launches made while
+ * sxl_enable_gemm_timing is on.  reset = 1 clears these counters. */
+int sxl_gemm_timers(sxl_ctx* ctx, double* out16, int reset);
 
 /* Diagnostics of the last density: [mu, N(mu), foe_steps, lambda_min,
  * lambda_max, GEMM launches so far, own kernel launches so far]. */

@@ -57,11 +57,20 @@ void ev_resolve(sxl_ctx* c) {
   for (auto& p : c->ev_pending) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
-      c->tc_launches += 1;
-      c->tc_ms += ms;
-      c->tc_mma_flops += p.mma_flops;
-      c->tc_alg_flops += p.alg_flops;
-      c->tc_f32_flops += p.f32_flops;
+      if (p.variant != 3) {  // tensor-core launches
+        c->tc_launches += 1;
+        c->tc_ms += ms;
+        c->tc_mma_flops += p.mma_flops;
+        c->tc_alg_flops += p.alg_flops;
+        c->tc_f32_flops += p.f32_flops;
+      }
+      if (p.variant >= 0 && p.variant < 4) {
+        double* v = c->tcv[p.variant];
+        v[0] += 1;
+        v[1] += ms;
+        v[2] += p.mma_flops;
+        v[3] += p.f32_flops;
+      }
     }
     c->ev_free.push_back(p.a);
     c->ev_free.push_back(p.b);
@@ -479,6 +488,7 @@ int sxl_create(const sxl_params* prm, void* stream, sxl_ctx** out) {
   c->N = NORB * p.n_atoms;
   c->Np = c->N;
   c->dup = nullptr;
+  c->tc_err = nullptr;
   c->diis_N = c->diis_F = c->diis_B = c->diis_coef = nullptr;
   c->diis_list = c->diis_flag = nullptr;
   c->diis_count = c->diis_head = 0;
@@ -499,6 +509,7 @@ int sxl_create(const sxl_params* prm, void* stream, sxl_ctx** out) {
   c->time_tc = false;
   c->tm_steps = c->tm_density = c->tm_forces = c->tm_krylov = c->tm_ranks = 0;
   c->tc_launches = c->tc_ms = c->tc_mma_flops = c->tc_alg_flops = c->tc_f32_flops = 0;
+  for (auto& v : c->tcv) v[0] = v[1] = v[2] = v[3] = 0;
   if (p.precision != SXL_FP64) {
     // the mixed-precision chain is provided by the tensor-core path
     int r = sxl_mixed_supported(c);
@@ -741,9 +752,9 @@ static int evaluate(sxl_ctx* c, double* en) {
   int rank = 0;
   SXL_TRY(krylov(c, n, c->p.krylov_rank, 0.0, c->Kf, nullptr, &rank));
   cudaEvent_t k1 = phase_mark(c);
-  c->ph_pending.push_back({d0, d1, 0.0, 0.0, 0.0});
-  c->ph_pending.push_back({f0, f1, 1.0, 0.0, 0.0});
-  c->ph_pending.push_back({k0, k1, 2.0, (double)rank, 0.0});
+  c->ph_pending.push_back({d0, d1, 0.0, 0.0, 0.0, -1});
+  c->ph_pending.push_back({f0, f1, 1.0, 0.0, 0.0, -1});
+  c->ph_pending.push_back({k0, k1, 2.0, (double)rank, 0.0, -1});
   c->evaluated = true;
   return SXL_OK;
 }
@@ -902,6 +913,7 @@ int sxl_mixed_gemm(sxl_ctx* c, const double* A, const double* B, const double* E
                    double alpha, double beta, double gamma, int sym, int split) {
   if (!c || !A || !B || !C) return SXL_E_ARG;
   if (c->p.precision == SXL_FP64) return sxl_fail(c, SXL_E_STATE, "context is fp64");
+  if (split < 0 || split > 2) return sxl_fail(c, SXL_E_ARG, "split must be 0, 1 or 2");
   // the product runs in the density chain's buffers: the density is gone
   c->have_density = false;
   SXL_TRY(mixed_gemm_test(c, A, B, E, C, alpha, beta, gamma, sym, split));
@@ -935,7 +947,19 @@ int sxl_timers(sxl_ctx* c, double* out, int reset) {
   if (reset) {
     c->tm_steps = c->tm_density = c->tm_forces = c->tm_krylov = c->tm_ranks = 0;
     c->tc_launches = c->tc_ms = c->tc_mma_flops = c->tc_alg_flops = c->tc_f32_flops = 0;
+    for (auto& v : c->tcv) v[0] = v[1] = v[2] = v[3] = 0;
   }
+  return SXL_OK;
+}
+
+int sxl_gemm_timers(sxl_ctx* c, double* out16, int reset) {
+  if (!c || !out16) return SXL_E_ARG;
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  ev_resolve(c);
+  for (int v = 0; v < 4; ++v)
+    for (int j = 0; j < 4; ++j) out16[4 * v + j] = c->tcv[v][j];
+  if (reset)
+    for (auto& v : c->tcv) v[0] = v[1] = v[2] = v[3] = 0;
   return SXL_OK;
 }
 

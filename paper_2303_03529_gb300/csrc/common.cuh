@@ -68,6 +68,7 @@ struct sxl_ctx {
   // padding orbitals form a decoupled diagonal block at the upper spectral
   // bound (empty states)
   int Np;
+  int* tc_err;            // the device's tensor-core wait-timeout flag (mixed.cu)
   double* dup;            // 2 x Np perturbation (zero on the padding)
   MatH hU, hS, hQ, hX0, hX1, hP, hSm, hdTa, hdTb, hG1;
   std::vector<MatH> hT, hY;
@@ -88,6 +89,7 @@ struct sxl_ctx {
   double *du;                   // 2N perturbation (scaled) per orbital
   double *dh;                   // 2 N_at
   double *red;                  // reduction scratch (>= 4096 doubles)
+#define MU_SHIFT_TRACES 3160      // red[+0..5]: Tr T, Tr T^2, Tr T^3 of T_nr per spin
   double *hred;                 // pinned host scratch (64 doubles)
 
   // Krylov
@@ -100,12 +102,14 @@ struct sxl_ctx {
   struct EvPair {
     cudaEvent_t a, b;
     double mma_flops, alg_flops, f32_flops;
+    int variant;  // GEMM form: 0 plain, 1 dual, 2 split (tensor cores), 3 fp64; -1 phase
   };
   bool time_tc;                      // per-launch timing of the tensor-core GEMM
   std::vector<cudaEvent_t> ev_free;  // recycled events
   std::vector<EvPair> ev_pending;    // recorded, not yet resolved
   double tm_steps, tm_density, tm_forces, tm_krylov, tm_ranks;
   double tc_launches, tc_ms, tc_mma_flops, tc_alg_flops, tc_f32_flops;
+  double tcv[4][4];                  // per GEMM form: launches, ms, MMA flops, product flops
   std::vector<EvPair> ph_pending;    // phase events: mma_flops = phase id
 };
 

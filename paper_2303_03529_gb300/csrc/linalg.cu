@@ -87,12 +87,29 @@ void gemm_f64(sxl_ctx* c, int batch, int n, const double* A, const double* B, do
               double alpha, const double* E, double beta, double gamma, bool sym) {
   int nt = (n + GB - 1) / GB;
   c->n_gemm++;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->time_tc) {
+    e0 = ev_get(c);
+    e1 = ev_get(c);
+    cudaEventRecord(e0, c->st);
+  }
   if (sym) {
     dim3 grid(nt * (nt + 1) / 2, batch);
     LAUNCH(k_gemm_f64<true>, grid, 256, 0, c->st, n, nt, A, B, C, E, alpha, beta, gamma);
   } else {
     dim3 grid(nt * nt, batch);
     LAUNCH(k_gemm_f64<false>, grid, 256, 0, c->st, n, nt, A, B, C, E, alpha, beta, gamma);
+  }
+  if (c->time_tc) {
+    cudaEventRecord(e1, c->st);
+    // 2 n flops per owned output element (symmetric results own the upper
+    // triangle); the tiles issued cover whole 64 x 64 blocks
+    const double nn = n;
+    const double owned = sym ? nn * (nn + 1) / 2 : nn * nn;
+    const double tiles = sym ? nt * (nt + 1) / 2.0 : (double)nt * nt;
+    const double issued = tiles * GB * GB * 2.0 * nt * GB;
+    const double f = 2.0 * nn * owned * batch;
+    c->ev_pending.push_back({e0, e1, issued * batch, f, f, 3});
   }
 }
 

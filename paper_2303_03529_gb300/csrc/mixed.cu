@@ -27,8 +27,10 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
+#include <mutex>
 
 #define TC_BM 128
 #define TC_BN 256
@@ -469,18 +471,24 @@ __global__ void __launch_bounds__(192, 1)
 
 // ---------------------------------------------------------------------------
 // host side: tensor maps and launch
-static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
-static int* g_tc_err = nullptr;
+// The driver's tensor-map encoder, looked up once; several host threads may
+// race to store the same pointer, which the atomic makes well defined.
+static std::atomic<PFN_cuTensorMapEncodeTiled_v12000> g_encode{nullptr};
+// One wait-timeout flag per device, shared by the contexts on that device
+// and created by the first of them.
+#define TC_MAX_DEV 64
+static int* g_tc_err[TC_MAX_DEV];
+static std::mutex g_tc_err_mutex;
 
 static int get_encode(sxl_ctx* c) {
-  if (g_encode) return SXL_OK;
+  if (g_encode.load(std::memory_order_acquire)) return SXL_OK;
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult q;
   cudaError_t e =
       cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
   if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
     return sxl_fail(c, SXL_E_UNSUPPORTED, "cuTensorMapEncodeTiled not available");
-  g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  g_encode.store((PFN_cuTensorMapEncodeTiled_v12000)fn, std::memory_order_release);
   return SXL_OK;
 }
 
@@ -490,7 +498,7 @@ static int make_map(sxl_ctx* c, CUtensorMap* m, const uint16_t* base, int n, int
   cuuint64_t strides[1] = {(cuuint64_t)n * 2};
   cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = g_encode(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+  CUresult r = g_encode.load(std::memory_order_acquire)(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
                         2, (void*)base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         bk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -531,7 +539,7 @@ static int launch_tc(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a) {
     const double mma = 2.0 * tiles * 2.0 * TC_BM * MT * TC_BN * kdim * (SPLIT ? 3.0 : 1.0);
     const double owned = a.sym ? n * (n + 1) / 2 : n * n;
     const double f32 = 2.0 * 2.0 * owned * kdim;  // both spins, 2 K per owned element
-    c->ev_pending.push_back({e0, e1, mma, f32 * (SPLIT ? 3.0 : 1.0), f32});
+    c->ev_pending.push_back({e0, e1, mma, f32 * (SPLIT ? 3.0 : 1.0), f32, DUAL ? 1 : (SPLIT ? 2 : 0)});
   }
   return SXL_OK;
 }
@@ -583,7 +591,7 @@ static int gemm_tc_range(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C
   a.Chi = C.hi;
   a.Clo = C.lo;
   a.sym = sym ? 1 : 0;
-  a.err = g_tc_err;
+  a.err = c->tc_err;
   c->n_gemm++;
   if (split) {
     if (bk == 64) return bf16 ? launch_tc<true, true, 64>(c, maps, a) : launch_tc<false, true, 64>(c, maps, a);
@@ -655,7 +663,7 @@ int gemm_tc_dual(sxl_ctx* c, const MatH& A1, const MatH& B1, const MatH& A2, con
   a.Chi = C.hi;
   a.Clo = C.lo;
   a.sym = sym ? 1 : 0;
-  a.err = g_tc_err;
+  a.err = c->tc_err;
   c->n_gemm++;
   return bf16 ? launch_tc<true, false, 64, 2, true>(c, maps, a)
               : launch_tc<false, false, 64, 2, true>(c, maps, a);
@@ -947,9 +955,16 @@ int sxl_mixed_supported(sxl_ctx* c) {
   CUDA_TRY(c, cudaGetDeviceProperties(&prop, dev));
   if (prop.major < 10) return sxl_fail(c, SXL_E_UNSUPPORTED, "tcgen05 needs compute capability 10.x");
   SXL_TRY(get_encode(c));
-  if (!g_tc_err) {
-    CUDA_TRY(c, cudaMalloc((void**)&g_tc_err, sizeof(int)));
-    CUDA_TRY(c, cudaMemset(g_tc_err, 0, sizeof(int)));
+  if (dev < 0 || dev >= TC_MAX_DEV) return sxl_fail(c, SXL_E_UNSUPPORTED, "device index too large");
+  {
+    std::lock_guard<std::mutex> lock(g_tc_err_mutex);
+    if (!g_tc_err[dev]) {
+      int* f = nullptr;
+      CUDA_TRY(c, cudaMalloc((void**)&f, sizeof(int)));
+      CUDA_TRY(c, cudaMemset(f, 0, sizeof(int)));
+      g_tc_err[dev] = f;
+    }
+    c->tc_err = g_tc_err[dev];
   }
   MatH* ms[] = {&c->hU, &c->hS, &c->hQ, &c->hX0, &c->hX1, &c->hP, &c->hSm, &c->hdTa, &c->hdTb, &c->hG1,
                 &c->hTeff};
@@ -978,8 +993,8 @@ void sxl_mixed_free(sxl_ctx* c) {
 
 int tc_error_flag(sxl_ctx* c, int* flag) {
   *flag = 0;
-  if (!g_tc_err) return SXL_OK;
-  CUDA_TRY(c, cudaMemcpyAsync(flag, g_tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  if (!c->tc_err) return SXL_OK;
+  CUDA_TRY(c, cudaMemcpyAsync(flag, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   return SXL_OK;
 }
@@ -1004,6 +1019,55 @@ static int ensure_chain_h(sxl_ctx* c, int nr) {
 }
 
 static double tanh5(double u) { return u - u * u * u / 3.0 + 2.0 * std::pow(u, 5) / 15.0; }
+
+// Per spin over the n real rows (2n-vectors indexed spin * n + row):
+// out[s] = sum_i T_ii and out[2 + s] = sum_i (T^2)_ii = sum_ij T_ij^2.
+__global__ void k_trace_stats(int n, const double* __restrict__ diagT,
+                              const double* __restrict__ rowsq, double* out) {
+  __shared__ double sa[256], sb[256];
+  const int s = blockIdx.x;
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    a += diagT[(size_t)s * n + i];
+    b += rowsq[(size_t)s * n + i];
+  }
+  sa[threadIdx.x] = a;
+  sb[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sa[threadIdx.x] += sa[threadIdx.x + o];
+      sb[threadIdx.x] += sb[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[s] = sa[0];
+    out[2 + s] = sb[0];
+  }
+}
+
+// part[b] = partial sums of <A, B> over the real n x n block of spin
+// blockIdx.y (matrices np x np); A and B symmetric (hi, lo) pairs
+template <bool BF16>
+__global__ void k_dot_block_partial(int n, int np, const uint16_t* ah, const uint16_t* al,
+                                    const uint16_t* bh, const uint16_t* bl, double* part) {
+  __shared__ double sm[256];
+  const size_t base = (size_t)blockIdx.y * np * np;
+  double s = 0.0;
+  const long long len = (long long)n * n;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < len; i += 256LL * gridDim.x) {
+    const size_t e = base + (size_t)(i / n) * np + (size_t)(i % n);
+    s += ld_hl_d<BF16>(ah, al, e) * ld_hl_d<BF16>(bh, bl, e);
+  }
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = sm[0];
+}
 
 // Same recursion as the fp64 form (see api.cu), on tensor cores.
 int foe_mixed(sxl_ctx* c, double mu, double* stats_dev) {
@@ -1076,6 +1140,9 @@ int foe_mixed(sxl_ctx* c, double mu, double* stats_dev) {
   int wpb = 8, rows = 2 * N;
   DISPATCH(c, k_rowstats_h, (rows + wpb - 1) / wpb, 32 * wpb, 0, Np, N, c->hT[nr].hi,
            c->hT[nr].lo, c->diagT, c->rowsq);
+  // Tr T and Tr T^2 of the pass's own T (the entropy's correction for a
+  // later mu shift needs them; the shift overwrites diagT and rowsq)
+  LAUNCH(k_trace_stats, 2, 256, 0, c->st, N, c->diagT, c->rowsq, c->red + MU_SHIFT_TRACES);
   small_kernels_density(c, c->q, stats_dev);
   return SXL_OK;
 }
@@ -1095,6 +1162,11 @@ int mu_shift_mixed(sxl_ctx* c, double dmu, double* stats_dev) {
   const double sd = 0.5 * c->beta * dmu;
   const MatH& T = c->hT[c->nr];
   SXL_TRY(gemm_tc(c, T, T, c->hSm, 1.f, nullptr, 0.f, 0.f, true, true));       // T^2
+  // Tr T^3 = <T, T^2> per spin for the entropy's shift correction
+  DISPATCH(c, k_dot_block_partial, dim3(64, 2), 256, 0, N, c->Np, T.hi, T.lo, c->hSm.hi,
+           c->hSm.lo, c->red + 2048);
+  LAUNCH(k_sum_parts, 1, 256, 0, c->st, 64, c->red + 2048, c->red + MU_SHIFT_TRACES + 4);
+  LAUNCH(k_sum_parts, 1, 256, 0, c->st, 64, c->red + 2048 + 64, c->red + MU_SHIFT_TRACES + 5);
   symcombo_h(c, c->hP, sd * sd, &c->hSm, 0.5 * sd, &T, 0.0, nullptr, nullptr);  // s T + s^2 T^2
   SXL_TRY(gemm_tc(c, T, c->hP, c->hTeff, 1.f, &T, (float)(1.0 - sd * sd), (float)(-sd), true,
                   true));
@@ -1219,8 +1291,12 @@ int mixed_gemm_test(sxl_ctx* c, const double* A, const double* B, const double* 
   DISPATCH(c, k_split_f64, g, 256, 0, nn, A, c->hU.hi, c->hU.lo);
   DISPATCH(c, k_split_f64, g, 256, 0, nn, B, c->hS.hi, c->hS.lo);
   if (E) DISPATCH(c, k_split_f64, g, 256, 0, nn, E, c->hQ.hi, c->hQ.lo);
-  SXL_TRY(gemm_tc(c, c->hU, c->hS, c->hG1, (float)alpha, E ? &c->hQ : nullptr, (float)beta,
-                  (float)gamma, sym != 0, split != 0));
+  if (split == 2)  // dual form: A B^T + B A^T over the concatenated K
+    SXL_TRY(gemm_tc_dual(c, c->hU, c->hS, c->hS, c->hU, c->hG1, (float)alpha,
+                         E ? &c->hQ : nullptr, (float)beta, (float)gamma, sym != 0));
+  else
+    SXL_TRY(gemm_tc(c, c->hU, c->hS, c->hG1, (float)alpha, E ? &c->hQ : nullptr, (float)beta,
+                    (float)gamma, sym != 0, split != 0));
   DISPATCH(c, k_join_f64, g, 256, 0, nn, c->hG1.hi, c->hG1.lo, C);
   return SXL_OK;
 }
@@ -1244,9 +1320,13 @@ static __device__ __align__(256) uint16_t g_noalloc_scratch[8 * NOALLOC_MAT];
 static __device__ __align__(256) int g_noalloc_err;
 
 #define NOALLOC_MAX_DEV 64
-static bool g_noalloc_ready[NOALLOC_MAX_DEV];
+// Set-up state per device.  Host threads making their first call on a
+// device at the same time serialize on the mutex; the ready flag is read
+// without it afterwards (release/acquire orders the pointers before it).
+static std::atomic<bool> g_noalloc_ready[NOALLOC_MAX_DEV];
 static uint16_t* g_noalloc_ptr[NOALLOC_MAX_DEV];
 static int* g_noalloc_err_ptr[NOALLOC_MAX_DEV];
+static std::mutex g_noalloc_mutex;
 
 template <bool BF16, bool SPLIT>
 static cudaError_t noalloc_attr() {
@@ -1258,7 +1338,9 @@ static cudaError_t noalloc_attr() {
 // addresses of the file-scope arrays (in host code their names are only
 // host-side stand-ins) and the shared-memory opt-in of the GEMM kernels.
 static int noalloc_setup(int dev) {
-  if (g_noalloc_ready[dev]) return SXL_OK;
+  if (g_noalloc_ready[dev].load(std::memory_order_acquire)) return SXL_OK;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (g_noalloc_ready[dev].load(std::memory_order_acquire)) return SXL_OK;
   void* p = nullptr;
   if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SXL_E_CUDA;
   void* e = nullptr;
@@ -1266,18 +1348,18 @@ static int noalloc_setup(int dev) {
   if (noalloc_attr<false, false>() != cudaSuccess || noalloc_attr<false, true>() != cudaSuccess ||
       noalloc_attr<true, false>() != cudaSuccess || noalloc_attr<true, true>() != cudaSuccess)
     return SXL_E_CUDA;
-  if (!g_encode) {
+  if (!g_encode.load(std::memory_order_acquire)) {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
                                          &q) != cudaSuccess ||
         q != cudaDriverEntryPointSuccess || !fn)
       return SXL_E_UNSUPPORTED;
-    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    g_encode.store((PFN_cuTensorMapEncodeTiled_v12000)fn, std::memory_order_release);
   }
   g_noalloc_ptr[dev] = (uint16_t*)p;
   g_noalloc_err_ptr[dev] = (int*)e;
-  g_noalloc_ready[dev] = true;
+  g_noalloc_ready[dev].store(true, std::memory_order_release);
   return SXL_OK;
 }
 
@@ -1286,7 +1368,7 @@ static int noalloc_map(CUtensorMap* m, const uint16_t* base, int n, int box_rows
   cuuint64_t strides[1] = {(cuuint64_t)n * 2};
   cuuint32_t box[2] = {TC_BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = g_encode(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+  CUresult r = g_encode.load(std::memory_order_acquire)(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
                         2, (void*)base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -1393,14 +1475,25 @@ __global__ void k_dot_hl_partial(long long len, const uint16_t* ah, const uint16
 }
 // sum_a s(f_a) = -N ln 2 - Tr ln cosh(Y) + Tr(Y T) per spin, from the
 // log-determinants of the chain (ld) and Tr(Y T) = 2^nr (<U, T> + <delta(U), T>)
+// A mu shift by dmu on top of the chain (sh = beta dmu / 2, T_eff of
+// mu_shift_mixed) leaves the chain's log-determinants at the pass's mu,
+// while the exact entropy wants them at the shifted one; per spin the
+// difference is
+//   sum_a [ln cosh y_a - ln cosh (y_a - sh)] - sh Tr T_eff
+//     = sh^2 / 2 Tr(I - T^2) + 2 sh^3 / 3 Tr(T - T^3) + O(sh^4)
+// with T the pass's own T_nr (tr: Tr T, Tr T^2, Tr T^3 per spin over the
+// nreal real states; the padding states are saturated and add nothing).
 __global__ void k_entropy_combine(int N, int nr, const double* ld, const double* dots, double* out,
-                                  const double* corr, double wcorr) {
+                                  const double* corr, double wcorr, double sh, int nreal,
+                                  const double* tr) {
   if (threadIdx.x != 0) return;
   double tot = 0.0;
   for (int s = 0; s < 2; ++s) {
     double v = -N * 0.69314718055994531 + ldexp(1.0, nr - 1) * ld[s] +
                ldexp(1.0, nr) * (dots[s] + wcorr * corr[s]);
     for (int k = 0; k < nr; ++k) v += ldexp(1.0, nr - 1 - k) * ld[2 * (k + 1) + s];
+    if (sh != 0.0)
+      v += 0.5 * sh * sh * (nreal - tr[2 + s]) + (2.0 / 3.0) * sh * sh * sh * (tr[s] - tr[4 + s]);
     tot += v;
   }
   out[0] = tot;
@@ -1472,6 +1565,7 @@ int entropy_mixed(sxl_ctx* c, double* out_dev) {
       LAUNCH(k_sum_parts, 1, 256, 0, c->st, 128, c->red + 2048, corr + s);
     }
   }
-  LAUNCH(k_entropy_combine, 1, 32, 0, c->st, N, nr, ld, dots, out_dev, corr, wcorr);
+  LAUNCH(k_entropy_combine, 1, 32, 0, c->st, N, nr, ld, dots, out_dev, corr, wcorr,
+         c->teff_valid ? c->fo_h : 0.0, c->N, c->red + MU_SHIFT_TRACES);
   return SXL_OK;
 }

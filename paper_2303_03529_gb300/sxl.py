@@ -85,6 +85,7 @@ EXPORTS = {
     "sxl_get_derived_host": (_i, [_p, _p, _p]),
     "sxl_timers": (_i, [_p, _p, _i]),
     "sxl_enable_gemm_timing": (_i, [_p, _i]),
+    "sxl_gemm_timers": (_i, [_p, _p, _i]),
     "sxl_mixed_gemm_noalloc": (_i, [_i, _i, _p, _p, _p, _p, _d, _d, _d, _i, _i, _p]),
 }
 
@@ -333,7 +334,9 @@ class Context:
         return out, its[:nsteps].copy()
 
     def mixed_gemm(self, A, B, E=None, alpha=1.0, beta=0.0, gamma=0.0, sym=False, split=True):
-        """C = alpha A B^T + beta E + gamma I on the tensor-core path (2 x N x N)."""
+        """C = alpha A B^T + beta E + gamma I on the tensor-core path (2 x N x N);
+        split=True/1 three-product form, False/0 hi parts only, 2 the dual form
+        C = alpha (A B^T + B A^T) + beta E + gamma I."""
         A, B = self._dev(A), self._dev(B)
         E = self._dev(E) if E is not None else None
         C = self._new(2, self.N, self.N)
@@ -361,6 +364,16 @@ class Context:
         keys = ("steps", "density_ms", "forces_ms", "krylov_ms", "ranks", "tc_launches",
                 "tc_ms", "tc_mma_flops", "tc_alg_flops", "tc_fp32_flops")
         return dict(zip(keys, out.tolist()))
+
+    def gemm_timers(self, reset=False):
+        """Per product form ("plain", "dual", "split", "fp64"): launches, ms,
+        issued_flops, product_flops (each product counted once)."""
+        out = np.zeros(16)
+        self._check(self.lib.sxl_gemm_timers(self.h, out.ctypes.data_as(_p), int(reset)),
+                    "sxl_gemm_timers")
+        keys = ("launches", "ms", "issued_flops", "product_flops")
+        return {name: dict(zip(keys, out[4 * v:4 * v + 4].tolist()))
+                for v, name in enumerate(("plain", "dual", "split", "fp64"))}
 
     def info(self):
         out = np.zeros(7)
@@ -418,13 +431,19 @@ def mixed_gemm_noalloc(n, precision, A, B, E=None, alpha=1.0, beta=0.0, gamma=0.
     import torch
     lib = load_library()
     nn = 2 * n * n
-    C = torch.empty(2, n, n, dtype=torch.float64, device="cuda")
-    st = stream if stream is not None else torch.cuda.current_stream()
-    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    rc = lib.sxl_mixed_gemm_noalloc(int(n), prec, _ptr(A, nn), _ptr(B, nn),
-                                    _ptr(E, nn) if E is not None else None, _ptr(C),
-                                    float(alpha), float(beta), float(gamma), int(sym), int(split),
-                                    _p(st.cuda_stream))
+    dev = A.device
+    for name, t in (("B", B), ("E", E)):
+        if t is not None and t.device != dev:
+            raise ValueError(f"{name} is on {t.device}, A on {dev}: all operands must share a device")
+    # the library works on the current device (its scratch and the stream's)
+    with torch.cuda.device(dev):
+        C = torch.empty(2, n, n, dtype=torch.float64, device=dev)
+        st = stream if stream is not None else torch.cuda.current_stream(dev)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        rc = lib.sxl_mixed_gemm_noalloc(int(n), prec, _ptr(A, nn), _ptr(B, nn),
+                                        _ptr(E, nn) if E is not None else None, _ptr(C),
+                                        float(alpha), float(beta), float(gamma), int(sym),
+                                        int(split), _p(st.cuda_stream))
     if rc != 0:
         raise SxlError(f"sxl_mixed_gemm_noalloc failed ({rc})")
     return C
