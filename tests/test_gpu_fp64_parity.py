@@ -116,9 +116,9 @@ def test_scf_fixed_point(lib):
 
 
 def test_xlbomd_trajectory_matches_oracle(lib):
-    """Ten sXL-BOMD steps from the SCF point (exact K0, rank 4): positions,
-    velocities, n, total energy without the entropy term and mu follow the
-    oracle step by step."""
+    """The 16-atom cell's full run, 100 sXL-BOMD steps from the SCF point
+    (exact K0, rank 4): positions, velocities, n, temperature, RMS(q - n)
+    and mu follow the oracle step by step."""
     w = wl.fe16()
     res = dynamics.scf(w.R, w.cell, w.n0, w.params, tol=1e-10)
     md = dynamics.XLBOMD(w.R, w.V, w.cell, res["n"], w.params, res["K0"], mu=res["mu"])
@@ -126,7 +126,7 @@ def test_xlbomd_trajectory_matches_oracle(lib):
     ctx.set_k0(res["K0"])
     nh = np.tile(res["n"], (w.params.kmax + 1, 1))
     ctx.set_state(w.R, w.V, nh, res["mu"])
-    for step in range(10):
+    for step in range(100):
         st_o = md.step()
         st = ctx.step(1)[0]
         R, V, nhg, mu = ctx.get_state()
