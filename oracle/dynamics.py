@@ -31,7 +31,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import electronic, energy, kernel, model
+from . import electronic, energy, general, kernel, model
 
 KB = 8.617333262e-5          # eV / K
 MVV_TO_EV = 103.642696562    # amu A^2 / fs^2 in eV
@@ -111,8 +111,11 @@ def scf(R, cell, n0, p, tol=1e-8, max_iter=200, rank=None, lin_mix=0.06,
 class XLBOMD:
     """State and time stepping of Eq. Integration."""
 
-    def __init__(self, R, V, cell, n_star, p, K0, mu=None):
+    def __init__(self, R, V, cell, n_star, p, K0, mu=None, general_model=False):
+        """general_model: the non-orthogonal, l-resolved model of
+        oracle/general.py in place of the orthogonal per-atom one."""
         self.p = p
+        self.general_model = general_model
         self.cell = np.asarray(cell, dtype=np.float64)
         self.R = np.array(R, dtype=np.float64)
         self.V = np.array(V, dtype=np.float64)
@@ -126,11 +129,18 @@ class XLBOMD:
         H0 = model.build_h0(self.R, self.cell, p)
         G = model.gamma_matrix(self.R, self.cell, p)
         n = self.nhist[0]
-        self.dens = electronic.Density(H0, G, n, p, mu_guess=self.mu)
+        if self.general_model:
+            S = general.overlap(self.R, self.cell, p)
+            self.dens = general.GDensity(H0, S, G, n, p, mu_guess=self.mu)
+            self.F = general.forces(self.dens, self.R, self.cell)
+            self.E = general.shadow_energy(self.dens, H0,
+                                           model.repulsive_energy(self.R, self.cell, p))
+        else:
+            self.dens = electronic.Density(H0, G, n, p, mu_guess=self.mu)
+            self.F = energy.forces(self.dens, self.R, self.cell)
+            self.E = energy.shadow_energy(self.dens, H0,
+                                          model.repulsive_energy(self.R, self.cell, p))
         self.mu = self.dens.mu
-        self.F = energy.forces(self.dens, self.R, self.cell)
-        self.E = energy.shadow_energy(self.dens, H0,
-                                      model.repulsive_energy(self.R, self.cell, p))
         self.Kf, self.kinfo = kernel.krylov_kernel(self.dens, self.K0, p.krylov_rank)
 
     def accel(self):

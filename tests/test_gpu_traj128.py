@@ -1,0 +1,68 @@
+"""200 sXL-BOMD steps of the 128-atom cell (4x4x4 bcc, 1152 orbitals x 2
+spins, Krylov rank 6, dt 0.5 fs) in the FP64 form against the oracle's run
+of the same trajectory, stored by tests/golden/make_traj128.py (which calls
+only oracle/).
+
+Both start at the oracle's SCF fixed point n* (all history slots n*, Sec.
+II.E) with K0 = J^{-1} evaluated exactly at n* (the library builds its own
+from 2 N_at responses).  Checked every step: total energy, temperature,
+RMS(q - n) and mu; at steps 50, 100 and 200 (stepping in chunks, state
+read back each time): positions, velocities and n.
+The two runs differ only by rounding, which the dynamics amplifies slowly
+over 100 fs; the tolerances leave room for that growth."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2303_03529_gb300 import workload as wl  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                      "fe128_traj_fp64.json")
+
+
+@pytest.fixture(scope="module")
+def sxl():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2303_03529_gb300 import sxl as s
+    return s
+
+
+def test_fe128_fp64_200_steps_against_oracle(sxl):
+    with open(GOLDEN) as f:
+        ref = json.load(f)
+    w = wl.fe128()
+    p, nat = w.params, w.n_atoms
+    n_star = np.array(ref["n_star"])
+    ctx = sxl.Context(p, nat, w.cell, "fp64")
+    _, mu = ctx.density(w.R, n_star, ref["mu_star"])
+    assert abs(mu - ref["mu_star"]) < 1e-9
+    ctx.build_exact_k0()
+    ctx.set_state(w.R, w.V, np.tile(n_star, (p.kmax + 1, 1)), mu)
+    stats, done = [], 0
+    for s in sorted(int(k) for k in ref["checkpoints"]):
+        stats.append(ctx.step(s - done))
+        done = s
+        R, V, nh, _ = ctx.get_state()
+        cp = ref["checkpoints"][str(s)]
+        dR = np.abs(R.cpu().numpy() - np.array(cp["R"])).max()
+        dV = np.abs(V.cpu().numpy() - np.array(cp["V"])).max()
+        dn = np.abs(nh[0].cpu().numpy() - np.array(cp["n"])).max()
+        print(f"fe128 fp64 step {s}: |dR| {dR:.2e} |dV| {dV:.2e} |dn| {dn:.2e}")
+        assert dR < 1e-9 and dV < 1e-10 and dn < 1e-8
+    st = np.concatenate(stats)
+    assert st.shape[0] == ref["steps"]
+    E, T, rms, mus = (np.array(ref["stats"][k]) for k in ("Etot", "T", "rms", "mu"))
+    dE = np.abs(st[:, 0] - E).max() / nat
+    print(f"fe128 fp64 200 steps: max |dE|/atom {dE:.2e} |dT| {np.abs(st[:, 1] - T).max():.2e} "
+          f"|drms| {np.abs(st[:, 2] - rms).max():.2e} |dmu| {np.abs(st[:, 3] - mus).max():.2e}")
+    assert dE < 1e-9
+    assert np.abs(st[:, 1] - T).max() < 1e-5
+    assert np.abs(st[:, 2] - rms).max() < 1e-9
+    assert np.abs(st[:, 3] - mus).max() < 1e-9
+    ctx.close()
