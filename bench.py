@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--n", type=int, default=4608, help="--gemm-only matrix size (9 N_at, N_at % 64 == 0)")
     ap.add_argument("--sym", action="store_true", help="--gemm-only: symmetric output")
     ap.add_argument("--reps", type=int, default=5, help="--gemm-only launches timed")
+    ap.add_argument("--torch-reference", action="store_true",
+                    help="--gemm-only: also time torch.matmul (cuBLAS) on the same operands")
     return ap.parse_args()
 
 
@@ -633,8 +635,9 @@ def run_gemm_only(args):
     if n % 576 != 0:
         raise SystemExit("--n must be 9 N_at with N_at a multiple of 64 (576, 1152, ...)")
     torch.cuda.set_device(0)
+    fp64 = args.precision == "fp64"
     ctx = sxl.Context(workload.ModelParams(), n // 9, [60.0, 60.0, 60.0],
-                      "bf16" if args.precision == "bf16" else "fp16")
+                      "fp64" if fp64 else ("bf16" if args.precision == "bf16" else "fp16"))
     g = torch.Generator(device="cuda").manual_seed(0)
     A = torch.randn(2, n, n, generator=g, device="cuda", dtype=torch.float64) / n ** 0.5
     sym = args.sym or args.variant == "dual"
@@ -643,21 +646,42 @@ def run_gemm_only(args):
     mode = {"plain": 0, "split": 1, "dual": 2}[args.variant]
     ctx.enable_gemm_timing(True)
     for _ in range(args.reps):
-        ctx.mixed_gemm(A, B, sym=sym, split=mode)
-    gt = ctx.gemm_timers(reset=True)[args.variant]
+        if fp64:
+            ctx.gemm_f64(A, B, sym=args.sym)
+        else:
+            ctx.mixed_gemm(A, B, sym=sym, split=mode)
+    form = "fp64" if fp64 else args.variant
+    gt = ctx.gemm_timers(reset=True)[form]
     ctx.close()
     peaks, src = measured_peaks()
     peak = peaks.get("bf16_tflops", 1900.0)
     ms = gt["ms"] / gt["launches"]
     ach = gt["product_flops"] / gt["launches"] / (ms / 1e3) / 1e12
-    print(json.dumps({"mode": "gemm-only", "variant": args.variant, "n": n, "sym": sym,
-                      "precision": args.precision, "launches": int(gt["launches"]),
-                      "ms_per_launch": round(ms, 4), "product_tflops": round(ach, 1),
-                      "issued_tflops": round(gt["issued_flops"] / gt["launches"] /
-                                             (ms / 1e3) / 1e12, 1),
-                      "frac_of_burst_peak": round(ach / peak, 4),
-                      "peak": f"{src} bf16_tflops (burst; the launches are timed alone)"}),
-          flush=True)
+    out = {"mode": "gemm-only", "variant": form, "n": n, "sym": sym if not fp64 else args.sym,
+           "precision": args.precision, "launches": int(gt["launches"]),
+           "ms_per_launch": round(ms, 4), "product_tflops": round(ach, 3),
+           "issued_tflops": round(gt["issued_flops"] / gt["launches"] / (ms / 1e3) / 1e12, 3)}
+    if not fp64:
+        out.update({"frac_of_burst_peak": round(ach / peak, 4),
+                    "peak": f"{src} bf16_tflops (burst; the launches are timed alone)"})
+    if args.torch_reference:
+        # cuBLAS on the same operands and dtype (the 16-bit forms: the hi
+        # parts, one batched product), best of reps, CUDA events
+        dt = torch.float64 if fp64 else (torch.bfloat16 if args.precision == "bf16"
+                                          else torch.float16)
+        a, b = A.to(dt), B.to(dt)
+        best = None
+        for _ in range(args.reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.bmm(a, b.transpose(1, 2))
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None or t < best else best
+        out["torch_bmm"] = {"dtype": str(dt).replace("torch.", ""), "ms": round(best, 4),
+                            "tflops": round(2 * 2 * n ** 3 / (best / 1e3) / 1e12, 3)}
+    print(json.dumps(out), flush=True)
 
 
 def main():

@@ -14,6 +14,9 @@
  * forces at constant n (Eq. EqMot) and advances R and n with the
  * dissipative modified Verlet scheme (Eq. Integration).
  *
+ * Extended-vector length: n2 = 2 N_at (per-atom model) or 2 N_at x 3
+ * (l_resolved = 1); every "2 N_at" below is n2 in the l-resolved model.
+ *
  * Conventions for every entry point:
  *   - Arrays are contiguous, row-major, float64.  Pointers named *_dev are
  *     device pointers, *_host are host pointers.  The caller owns every
@@ -90,6 +93,20 @@ typedef struct {
                                 SXL_FP64, 1e-6 N_e for the mixed forms)      */
   int    scf_keep_k0;        /* scf_solve: 0 = build the exact K0 = J^{-1} when the
                                 kernel mixer starts, 1 = keep the installed K0 */
+  /* Paper-general model (Sec. II.C, Sec. III.A); SXL_FP64 only.  All S0 = 0
+   * and l_resolved = 0 give the orthogonal per-atom model above.          */
+  double S0[10];             /* overlap integrals, same order as V0: S_ii = 1,
+                                S between atoms = Slater-Koster blocks of
+                                S0 exp(-s_decay (r - r0)) s(r); D = Z f(Z^T H Z) Z^T
+                                with Z^T S Z = I (Eq. D_min), Mulliken
+                                occupations sum_j D_ij S_ji, H = H0 +
+                                S o (v 1^T + 1 v^T) / 2                        */
+  double s_decay;            /* radial decay of the overlap integrals, 1/A      */
+  int    l_resolved;         /* 1: charges and spins per (atom, shell s/p/d),
+                                n = [n_up (N_at x 3); n_dn (N_at x 3)] and the
+                                spin shift sigma J_l s_{I,l} (Eq. nfromP);
+                                0: per atom with J = W / 2                     */
+  double J_l[3];             /* l-dependent Stoner parameters (s, p, d), eV    */
 } sxl_params;
 
 /* Create a context bound to the current CUDA device and `stream` (a
@@ -254,6 +271,15 @@ int sxl_batch_destroy(sxl_batch* batch);
  * (call sxl_density again before sxl_response or sxl_forces). */
 int sxl_mixed_gemm(sxl_ctx* ctx, const double* A_dev, const double* B_dev, const double* E_dev,
                    double* C_dev, double alpha, double beta, double gamma, int sym, int split);
+
+/* Diagnostic: the same product in fp64, C[b] = alpha A[b] B[b]^T + beta E[b]
+ * + gamma I (b = 0, 1; N x N device arrays, E may be NULL), through the
+ * library's fp64 GEMM, the product of every step of the SXL_FP64 chains.
+ * Any context; touches none of its buffers.  sym = 1 computes the upper
+ * tiles and mirrors them (valid only for a symmetric result).
+ * Synchronizes the context's stream. */
+int sxl_gemm_f64(sxl_ctx* ctx, const double* A_dev, const double* B_dev, const double* E_dev,
+                 double* C_dev, double alpha, double beta, double gamma, int sym);
 
 /* Allocation-free form of sxl_mixed_gemm, for callers that cannot call
  * cudaMalloc (for example code whose device memory is all handed out by its

@@ -128,7 +128,8 @@ static int foe_f64(sxl_ctx* c, double mu, double* stats_dev) {
   c->umax = c->scale * std::max(std::fabs(c->lam_max - mu), std::fabs(mu - c->lam_min));
   if (!(c->umax <= 1.2))
     return sxl_fail(c, SXL_E_ARG, "expansion start out of range (|U| > 1.2): raise foe_steps");
-  build_u_f64(c, c->H0, c->shift, mu, c->scale, c->U);
+  if (c->general) build_u_dense_f64(c, c->Hp, mu, c->scale, c->U);
+  else build_u_f64(c, c->H0, c->shift, mu, c->scale, c->U);
   gemm_f64(c, 2, N, c->U, c->U, c->S, 1.0, nullptr, 0.0, 0.0, true);
   gemm_f64(c, 2, N, c->S, c->S, c->Q, 2.0 / 15.0, c->S, -1.0 / 3.0, 1.0, true);
   gemm_f64(c, 2, N, c->U, c->Q, c->T[0], 1.0, nullptr, 0.0, 0.0, true);
@@ -206,11 +207,17 @@ static int build_model(sxl_ctx* c, const double* R, const double* n) {
   if (!c->h0_valid || std::memcmp(hR.data(), hC.data(), hR.size() * sizeof(double)) != 0) {
     launch_build_h0(c, R);
     launch_build_gamma(c, R);
+    if (c->general) SXL_TRY(general_overlap(c, R));
     CUDA_TRY(c, cudaMemcpyAsync(c->Rcur, R, 3 * c->nat * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     c->h0_valid = true;
   }
-  launch_spin_shift(c, n, c->shift);
-  lanczos_bounds(c, c->red);
+  if (c->general) {
+    // H_perp = Z H Z and its Gershgorin bounds
+    SXL_TRY(general_hamiltonian(c, n, c->red));
+  } else {
+    launch_spin_shift(c, n, c->shift);
+    lanczos_bounds(c, c->red);
+  }
   SXL_TRY(sync_host(c, c->red, 2));
   c->lam_min = c->hred[0];
   c->lam_max = c->hred[1];
@@ -275,8 +282,7 @@ static int density(sxl_ctx* c, const double* R, const double* n, double mu_guess
       return sxl_fail(c, SXL_E_NO_CONVERGENCE, "chemical potential search hit its iteration cap");
     if (err > 0) hi = mu; else lo = mu;
     // mixed forms: a remaining Newton step with beta |dmu| <= 0.1 is applied
-    // to the final T to second order (neglected term <= (beta dmu / 2)^3 / 3)
-    // instead of another pass.  The shift is repeated from T_nr with the
+    // to the final T to third order in beta dmu / 2 instead of another pass.  The shift is repeated from T_nr with the
     // accumulated dmu until |N - N_e| < tol (a Newton step in mu leaves
     // N'' dmu^2 / 2); if that does not settle, a full pass runs at the shifted
     // mu.  The response follows the shift to first order.
@@ -311,6 +317,7 @@ static int density(sxl_ctx* c, const double* R, const double* n, double mu_guess
     if (!(mn > lo && mn < hi)) mn = 0.5 * (lo + hi);
     mu = mn;
   }
+  if (c->general) SXL_TRY(general_finish_density(c));
   c->mu = mu;
   c->have_density = true;
   return SXL_OK;
@@ -318,6 +325,7 @@ static int density(sxl_ctx* c, const double* R, const double* n, double mu_guess
 
 static int response(sxl_ctx* c, const double* v, double* qv, double* dmu_dev) {
   if (!c->have_density) return sxl_fail(c, SXL_E_STATE, "no density: call sxl_density first");
+  if (c->general) return general_response(c, v, qv, dmu_dev);
   launch_spin_shift(c, v, c->dh);
   perturb_du(c, c->dh, c->du);
   if (c->p.precision != SXL_FP64) SXL_TRY(dmpt_mixed(c, c->du));
@@ -398,6 +406,24 @@ __global__ void k_energy_band(int N, const double* __restrict__ H0, double d0s, 
   if (threadIdx.x == 0) out[0] = 0.5 * (ttr - dots[0]) + 0.5 * (ttr - dots[1]) - 2.0 * sm[0];
 }
 
+// d[s] <- Tr H0 - 2 d[s] for both spins (turns <H0, D> into the <H0, T> the
+// band kernel expects, D = (I - T)/2)
+__global__ void k_band_dots_from_d(int N, const double* __restrict__ H0, double* d) {
+  __shared__ double sm[1024];
+  double tr = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tr += H0[(size_t)i * N + i];
+  sm[threadIdx.x] = tr;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    d[0] = sm[0] - 2.0 * d[0];
+    d[1] = sm[0] - 2.0 * d[1];
+  }
+}
+
 __global__ void k_entropy_combine_f64(int N, int nr, const double* ld, const double* dots,
                                       double* out) {
   if (threadIdx.x != 0) return;
@@ -433,11 +459,17 @@ static int entropy_f64(sxl_ctx* c, double* out_dev) {
 // forces at the current density; energies (6 doubles, host) if requested
 static int eval_forces(sxl_ctx* c, const double* R, const double* n, double* F, double* en) {
   double* erep = c->tmpv;  // nat doubles
-  launch_forces(c, R, n, c->q, F, erep);
+  if (c->general) SXL_TRY(general_forces(c, R, n, F, erep));
+  else launch_forces(c, R, n, c->q, F, erep);
   if (en) {
     const size_t nn = (size_t)c->N * c->N;
     double* d = c->red + 64;
-    if (c->p.precision != SXL_FP64) {
+    if (c->general) {
+      // <H0, D> per spin; the band kernel takes <H0, T> with D = (I - T)/2,
+      // so pass Tr H0 - 2 <H0, D> in its place (k_band_dots_from_d)
+      general_band_dots(c, d);
+      LAUNCH(k_band_dots_from_d, 1, 1024, 0, c->st, c->N, c->H0, d);
+    } else if (c->p.precision != SXL_FP64) {
       dot_h0_t_mixed(c, 0, d);
       dot_h0_t_mixed(c, 1, d + 1);
     } else {
@@ -446,7 +478,8 @@ static int eval_forces(sxl_ctx* c, const double* R, const double* n, double* F, 
     }
     LAUNCH(k_energy_band, 1, 1024, 0, c->st, c->N, c->H0, c->p.d0_s, c->p.d0_p, c->p.d0_d, d,
            d + 2);
-    energy_terms(c, n, erep, d + 3);
+    if (c->general) general_energy_terms(c, n, erep, d + 3);
+    else energy_terms(c, n, erep, d + 3);
     if (c->p.precision != SXL_FP64) SXL_TRY(entropy_mixed(c, d + 6));
     else SXL_TRY(entropy_f64(c, d + 6));
     SXL_TRY(sync_host(c, d + 2, 5));
@@ -481,6 +514,17 @@ int sxl_create(const sxl_params* prm, void* stream, sxl_ctx** out) {
     return SXL_E_ARG;
   if (p.foe_steps < 0 || p.foe_steps > 40) return SXL_E_ARG;
   if (!(p.n_elec_per_atom > 0 && p.n_elec_per_atom < 18)) return SXL_E_ARG;
+  bool general = p.l_resolved != 0;
+  for (int i = 0; i < 10; ++i) {
+    if (!std::isfinite(p.S0[i])) return SXL_E_ARG;
+    if (p.S0[i] != 0.0) general = true;
+  }
+  if (p.l_resolved != 0 && p.l_resolved != 1) return SXL_E_ARG;
+  if (general && !(p.s_decay > 0)) return SXL_E_ARG;
+  for (int i = 0; i < 3; ++i)
+    if (!std::isfinite(p.J_l[i])) return SXL_E_ARG;
+  // the paper-general model runs in the fp64 form only
+  if (general && p.precision != SXL_FP64) return SXL_E_UNSUPPORTED;
   sxl_ctx* c = new sxl_ctx();
   c->p = p;
   c->st = (cudaStream_t)stream;
@@ -493,7 +537,11 @@ int sxl_create(const sxl_params* prm, void* stream, sxl_ctx** out) {
   c->diis_list = c->diis_flag = nullptr;
   c->diis_count = c->diis_head = 0;
   c->bomd_ready = false;
-  c->n2 = 2 * p.n_atoms;
+  c->general = general;
+  c->G = p.l_resolved ? 3 : 1;
+  c->n2 = 2 * p.n_atoms * c->G;
+  c->Sb = c->Zb = c->Hp = c->Dg = c->Mg = nullptr;
+  c->vorb = c->dsd = c->chiS = c->av = nullptr;
   c->beta = 1.0 / p.kT;
   c->hist_head = 0;
   c->mu = NAN;
@@ -538,6 +586,7 @@ int sxl_create(const sxl_params* prm, void* stream, sxl_ctx** out) {
     cudaError_t e = cudaMallocHost((void**)&c->hred, 64 * sizeof(double));
     if (e != cudaSuccess) r = SXL_E_NOMEM;
   }
+  if (r == SXL_OK) r = general_alloc(c);
   if (r != SXL_OK) { sxl_destroy(c); return r; }
   r = sxl_set_k0(c, SXL_K0_MINUS_IDENTITY, nullptr);
   if (r != SXL_OK) { sxl_destroy(c); return r; }
@@ -559,6 +608,7 @@ int sxl_destroy(sxl_ctx* c) {
   for (double* p : c->T) cudaFree(p);
   for (double* p : c->Y) cudaFree(p);
   sxl_mixed_free(c);
+  general_free(c);
   diis_free(c);
   ev_resolve(c);
   for (cudaEvent_t e : c->ev_free) cudaEventDestroy(e);
@@ -571,8 +621,12 @@ int sxl_hamiltonian(sxl_ctx* c, const double* R, const double* n, double* H) {
   if (!c || !R || !n) return SXL_E_ARG;
   c->have_density = false;
   SXL_TRY(build_model(c, R, n));
-  // H_sigma = H0 + diag(shift_sigma): the U builder with mu = 0, scale = 1
-  if (H) build_u_f64(c, c->H0, c->shift, 0.0, 1.0, H);
+  // H_sigma = H0 + diag(shift_sigma): the U builder with mu = 0, scale = 1;
+  // the general model's H_sigma = H0 + S o (v 1^T + 1 v^T)/2 sits in Mg
+  if (H && c->general)
+    CUDA_TRY(c, cudaMemcpyAsync(H, c->Mg, 2 * (size_t)c->N * c->N * sizeof(double),
+                                cudaMemcpyDeviceToDevice, c->st));
+  else if (H) build_u_f64(c, c->H0, c->shift, 0.0, 1.0, H);
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   return SXL_OK;
 }
@@ -599,7 +653,9 @@ int sxl_density_matrix(sxl_ctx* c, double* D) {
   if (!c || !D) return SXL_E_ARG;
   if (!c->have_density) return sxl_fail(c, SXL_E_STATE, "no density");
   size_t nn = 2 * (size_t)c->N * c->N;
-  if (c->p.precision != SXL_FP64) density_matrix_mixed(c, D);
+  if (c->general)
+    CUDA_TRY(c, cudaMemcpyAsync(D, c->Dg, nn * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  else if (c->p.precision != SXL_FP64) density_matrix_mixed(c, D);
   else LAUNCH(k_d_from_t, (unsigned)((nn + 255) / 256), 256, 0, c->st, nn, c->T[c->nr], D, c->N);
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   return SXL_OK;
@@ -924,6 +980,14 @@ int sxl_mixed_gemm(sxl_ctx* c, const double* A, const double* B, const double* E
   return SXL_OK;
 }
 
+int sxl_gemm_f64(sxl_ctx* c, const double* A, const double* B, const double* E, double* C,
+                 double alpha, double beta, double gamma, int sym) {
+  if (!c || !A || !B || !C) return SXL_E_ARG;
+  gemm_f64(c, 2, c->N, A, B, C, alpha, E, beta, gamma, sym != 0);
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return SXL_OK;
+}
+
 int sxl_enable_gemm_timing(sxl_ctx* c, int on) {
   if (!c) return SXL_E_ARG;
   c->time_tc = on != 0;
@@ -947,7 +1011,6 @@ int sxl_timers(sxl_ctx* c, double* out, int reset) {
   if (reset) {
     c->tm_steps = c->tm_density = c->tm_forces = c->tm_krylov = c->tm_ranks = 0;
     c->tc_launches = c->tc_ms = c->tc_mma_flops = c->tc_alg_flops = c->tc_f32_flops = 0;
-    for (auto& v : c->tcv) v[0] = v[1] = v[2] = v[3] = 0;
   }
   return SXL_OK;
 }

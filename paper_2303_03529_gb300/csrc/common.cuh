@@ -92,6 +92,16 @@ struct sxl_ctx {
 #define MU_SHIFT_TRACES 3160      // red[+0..5]: Tr T, Tr T^2, Tr T^3 of T_nr per spin
   double *hred;                 // pinned host scratch (64 doubles)
 
+  // paper-general model (general.cu; fp64 form): overlap S, Z = S^{-1/2}
+  // (both stored twice, one copy per spin block of the batched GEMMs), the
+  // orthogonalized H_perp = Z H Z, the density matrices D = Z D_perp Z, the
+  // per-orbital potentials and the S-weighted diagonals
+  bool general;           // overlap or l-resolved charges in use
+  int G;                  // charge/spin groups per atom (1, or 3 shells)
+  double *Sb, *Zb, *Hp, *Dg, *Mg;   // 2 x N x N each
+  double *vorb;           // 2 N orbital potentials v^sigma_i
+  double *dsd, *chiS, *av;// 2 N: (D S)_ii, (Z chi Z S)_ii, (Z dT Z S)_ii
+
   // Krylov
   double *K0, *Vk, *FTk, *ftil, *cvec, *qv, *fv, *wvec, *Jm, *Jinv;
   int *ipiv;
@@ -158,6 +168,12 @@ void launch_spin_shift(sxl_ctx* c, const double* n, double* out);
 // Tsum_f64 / Tsum_h: T_up + T_dn source (one of them non-null)
 void launch_forces(sxl_ctx* c, const double* R, const double* n, const double* qspin,
                    double* F, double* erep_atom);
+// overlap S (identity on site) into Sout (N x N)
+void launch_build_overlap(sxl_ctx* c, const double* R, double* Sout);
+// general-model forces from Dsum = D_up + D_dn and M = sum_sigma D o (v_i + v_j)/2 - W
+// (N x N each) and per-atom totals qtot, ntot
+void launch_forces_general(sxl_ctx* c, const double* R, const double* Dsum, const double* M,
+                           const double* qtot, const double* ntot, double* F, double* erep_atom);
 
 // ---- linear algebra (linalg.cu) ---------------------------------------------
 // C[b] = alpha A[b] B[b]^T + beta E[b] + gamma I over `batch` square n x n
@@ -193,6 +209,27 @@ void md_drift(sxl_ctx* c, double* R, const double* V);
 void md_nupdate(sxl_ctx* c, int head_new);
 void md_kinetic(sxl_ctx* c, const double* V, double* out);
 void energy_terms(sxl_ctx* c, const double* n, const double* erep_atom, double* out);
+
+// ---- paper-general model (general.cu) -----------------------------------------
+int general_alloc(sxl_ctx* c);
+void general_free(sxl_ctx* c);
+// S and Z = S^{-1/2} at positions R (after H0 and gamma)
+int general_overlap(sxl_ctx* c, const double* R);
+// orbital potentials for n, H_perp = Z (H0 + S o (v 1^T + 1 v^T)/2) Z and its
+// Gershgorin bounds into out2_dev
+int general_hamiltonian(sxl_ctx* c, const double* n, double* out2_dev);
+// after the mu search: D = Z D_perp Z, q per (atom, group), the response's
+// S-weighted susceptibility diagonal
+int general_finish_density(sxl_ctx* c);
+// response of the chain to direction v: q_v (n2) and dmu (device scalar)
+int general_response(sxl_ctx* c, const double* v, double* qv, double* dmu_dev);
+// forces and the energy terms that differ from the orthogonal model
+int general_forces(sxl_ctx* c, const double* R, const double* n, double* F, double* erep_atom);
+void general_energy_terms(sxl_ctx* c, const double* n, const double* erep_atom, double* out3);
+void general_band_dots(sxl_ctx* c, double* out2);
+// fp64 U = scale (H_perp - mu I) (the general form's expansion start)
+void build_u_dense_f64(sxl_ctx* c, const double* Hp, double mu, double scale, double* U);
+int dmpt_f64_dense(sxl_ctx* c, double* dU);
 
 // ---- mixed-precision chain (mixed.cu) ----------------------------------------
 int sxl_mixed_supported(sxl_ctx* c);

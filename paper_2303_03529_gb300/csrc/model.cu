@@ -186,6 +186,7 @@ __global__ void k_build_h0(int nat, const double* __restrict__ R, ModelConst mc,
           if (b != a) blk[(size_t)b * N + a] += ((c_ell[a] + c_ell[b]) & 1) ? -e : e;
         }
     }
+    if (!H0f) continue;  // the overlap build keeps no fp32 copy
     float* blkf = H0f + (size_t)(NORB * K) * N + NORB * J;
     for (int a = 0; a < NORB; ++a)
       for (int b = 0; b < NORB; ++b) blkf[(size_t)a * N + b] = (float)blk[(size_t)a * N + b];
@@ -209,6 +210,21 @@ void launch_build_h0(sxl_ctx* c, const double* R) {
   LAUNCH(k_build_h0, c->nat, 256, 0, c->st, c->nat, R, mc, c->H0, c->H0f);
   int wpb = 8;
   LAUNCH(k_rowabs, (c->N + wpb - 1) / wpb, 32 * wpb, 0, c->st, c->N, c->H0, c->h0abs);
+}
+
+// The overlap has the Hamiltonian's structure: on-site identity and the
+// Slater-Koster table of the overlap integrals S0 with their own decay.
+static ModelConst overlap_const(const sxl_params& p) {
+  ModelConst m = model_const(p);
+  m.eps[0] = m.eps[1] = m.eps[2] = 1.0;
+  for (int i = 0; i < 10; ++i) m.V0[i] = p.S0[i];
+  m.q_decay = p.s_decay;
+  return m;
+}
+
+void launch_build_overlap(sxl_ctx* c, const double* R, double* Sout) {
+  LAUNCH(k_build_h0, c->nat, 256, 0, c->st, c->nat, R, overlap_const(c->p), Sout,
+         (float*)nullptr);
 }
 
 // gamma_IJ = k / sqrt(r^2 + (k/U)^2), minimum image, gamma_II = U
@@ -394,4 +410,99 @@ void launch_forces(sxl_ctx* c, const double* R, const double* n, const double* q
     TsumH<false> ts{T.hi, T.lo, npp, (size_t)c->Np};
     LAUNCH(k_forces<TsumH<false>>, c->nat, 256, 0, c->st, c->nat, R, mc, ts, n, qspin, F, erep_atom);
   }
+}
+
+// ---------------------------------------------------------------------------
+// Forces of the general model (non-orthogonal basis), block per atom K:
+//   F_K += 2 sum_{J != K, images} sum_ab [Dsum_{Ka,Jb} dE_ab/dd + M_{Ka,Jb} dS_ab/dd]
+// with M = sum_sigma D o (v_i + v_j)/2 - W (the overlap inside the Mulliken
+// occupations and the normalization's energy-weighted matrix), the
+// repulsion and the Coulomb term on the per-atom totals qtot, ntot.
+__global__ void __launch_bounds__(256) k_forces_general(
+    int nat, const double* __restrict__ R, ModelConst mh, ModelConst ms,
+    const double* __restrict__ Dsum, const double* __restrict__ Mw,
+    const double* __restrict__ qtot, const double* __restrict__ ntot, double* __restrict__ F,
+    double* __restrict__ erep) {
+  const int K = blockIdx.x;
+  const size_t N = (size_t)nat * NORB;
+  double fx = 0.0, fy = 0.0, fz = 0.0, er = 0.0;
+  const double Kx = R[3 * K], Ky = R[3 * K + 1], Kz = R[3 * K + 2];
+  for (int J = threadIdx.x; J < nat; J += blockDim.x) {
+    if (J == K) continue;
+    double dx0 = min_image(R[3 * J] - Kx, mh.cell[0]);
+    double dy0 = min_image(R[3 * J + 1] - Ky, mh.cell[1]);
+    double dz0 = min_image(R[3 * J + 2] - Kz, mh.cell[2]);
+    for (int s = 0; s < 27; ++s) {
+      const double ex = dx0 + (s / 9 - 1) * mh.cell[0];
+      const double ey = dy0 + ((s / 3) % 3 - 1) * mh.cell[1];
+      const double ez = dz0 + (s % 3 - 1) * mh.cell[2];
+      if (ex * ex + ey * ey + ez * ez >= mh.r_cut * mh.r_cut) continue;
+#pragma unroll 1
+      for (int dir = 0; dir < 3; ++dir) {
+        Dual1 dx(ex, dir == 0 ? 1.0 : 0.0), dy(ey, dir == 1 ? 1.0 : 0.0), dz(ez, dir == 2 ? 1.0 : 0.0);
+        Dual1 l, m, nn, radh, rads, r;
+        bond_setup<Dual1>(dx, dy, dz, mh, l, m, nn, radh, r);
+        rads = dexp(-ms.q_decay * (r - ms.r0)) * switch_fn<Dual1>(r, ms);
+        double g = 0.0;
+#pragma unroll 1
+        for (int a = 0; a < NORB; ++a)
+#pragma unroll 1
+          for (int b = a; b < NORB; ++b) {
+            const int key = a == 0 ? b : 10 * a + (b - a);
+            const Dual1 E = radh * sk_upper<Dual1>(key, l, m, nn, mh.V0);
+            const Dual1 Sv = rads * sk_upper<Dual1>(key, l, m, nn, ms.V0);
+            const size_t ij = (size_t)(NORB * K + a) * N + (size_t)(NORB * J + b);
+            double wd = Dsum[ij], wm = Mw[ij];
+            if (b != a) {
+              const size_t ji = (size_t)(NORB * K + b) * N + (size_t)(NORB * J + a);
+              const double sg = ((c_ell[a] + c_ell[b]) & 1) ? -1.0 : 1.0;
+              wd += sg * Dsum[ji];
+              wm += sg * Mw[ji];
+            }
+            g += 2.0 * (wd * E.g + wm * Sv.g);
+          }
+        if (mh.rep_A != 0.0) {
+          Dual1 phi = mh.rep_A * dexp(-mh.rep_b * (r - mh.r0)) * switch_fn<Dual1>(r, mh);
+          g += phi.g;
+          if (dir == 0) er += 0.5 * phi.v;
+        }
+        if (dir == 0) fx += g;
+        else if (dir == 1) fy += g;
+        else fz += g;
+      }
+    }
+  }
+  const double a_K = 2.0 * qtot[K] - ntot[K];
+  const double b_K = ntot[K];
+  const double ak2 = (mh.ck / mh.U) * (mh.ck / mh.U);
+  for (int J = threadIdx.x; J < nat; J += blockDim.x) {
+    if (J == K) continue;
+    double dx = min_image(R[3 * J] - Kx, mh.cell[0]);
+    double dy = min_image(R[3 * J + 1] - Ky, mh.cell[1]);
+    double dz = min_image(R[3 * J + 2] - Kz, mh.cell[2]);
+    double gm = mh.ck / sqrt(dx * dx + dy * dy + dz * dz + ak2);
+    double a_J = 2.0 * qtot[J] - ntot[J];
+    double b_J = ntot[J];
+    double w = 0.5 * gm * gm * gm / (mh.ck * mh.ck) * (a_J * b_K + a_K * b_J);
+    fx -= w * dx; fy -= w * dy; fz -= w * dz;
+  }
+  __shared__ double red[4][256];
+  red[0][threadIdx.x] = fx; red[1][threadIdx.x] = fy; red[2][threadIdx.x] = fz;
+  red[3][threadIdx.x] = er;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int k = 0; k < 4; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    F[3 * K] = red[0][0]; F[3 * K + 1] = red[1][0]; F[3 * K + 2] = red[2][0];
+    erep[K] = red[3][0];
+  }
+}
+
+void launch_forces_general(sxl_ctx* c, const double* R, const double* Dsum, const double* M,
+                           const double* qtot, const double* ntot, double* F, double* erep_atom) {
+  LAUNCH(k_forces_general, c->nat, 256, 0, c->st, c->nat, R, model_const(c->p),
+         overlap_const(c->p), Dsum, M, qtot, ntot, F, erep_atom);
 }

@@ -42,6 +42,7 @@ class Params(ctypes.Structure):
         ("kappa", _d), ("alpha", _d), ("c", _d * 10),
         ("precision", _i), ("foe_steps", _i), ("foe_u_max", _d),
         ("mu_max_iter", _i), ("mu_tol", _d), ("scf_keep_k0", _i),
+        ("S0", _d * 10), ("s_decay", _d), ("l_resolved", _i), ("J_l", _d * 3),
     ]
 
 
@@ -86,6 +87,7 @@ EXPORTS = {
     "sxl_timers": (_i, [_p, _p, _i]),
     "sxl_enable_gemm_timing": (_i, [_p, _i]),
     "sxl_gemm_timers": (_i, [_p, _p, _i]),
+    "sxl_gemm_f64": (_i, [_p, _p, _p, _p, _p, _d, _d, _d, _i]),
     "sxl_mixed_gemm_noalloc": (_i, [_i, _i, _p, _p, _p, _p, _d, _d, _d, _i, _i, _p]),
 }
 
@@ -136,6 +138,10 @@ def make_params(mp, n_atoms: int, cell, precision="fp64", foe_steps=0, foe_u_max
     p.mu_max_iter = int(mu_max_iter)
     p.mu_tol = float(mu_tol)
     p.scf_keep_k0 = int(scf_keep_k0)
+    p.S0[:] = [float(x) for x in getattr(mp, "S0", (0.0,) * 10)]
+    p.s_decay = float(getattr(mp, "s_decay", mp.q_decay))
+    p.l_resolved = int(bool(getattr(mp, "l_resolved", False)))
+    p.J_l[:] = [float(x) for x in getattr(mp, "J_l", (0.5 * mp.W,) * 3)]
     return p
 
 
@@ -160,7 +166,8 @@ class Context:
         self.lib = load_library()
         self.nat = int(n_atoms)
         self.N = 9 * self.nat
-        self.n2 = 2 * self.nat
+        # extended-vector length: per atom, or per (atom, shell) when l-resolved
+        self.n2 = 2 * self.nat * (3 if getattr(mp, "l_resolved", False) else 1)
         self.kmax = int(mp.kmax)
         self.params = make_params(mp, n_atoms, cell, precision, **kw)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -347,6 +354,19 @@ class Context:
                                             int(split)), "sxl_mixed_gemm")
         return C
 
+    def gemm_f64(self, A, B, E=None, alpha=1.0, beta=0.0, gamma=0.0, sym=False):
+        """C = alpha A B^T + beta E + gamma I in fp64 (2 x N x N), the fp64
+        form's product."""
+        A, B = self._dev(A), self._dev(B)
+        E = self._dev(E) if E is not None else None
+        C = self._new(2, self.N, self.N)
+        nn = 2 * self.N * self.N
+        self._check(self.lib.sxl_gemm_f64(self.h, _ptr(A, nn), _ptr(B, nn),
+                                          _ptr(E, nn) if E is not None else None, _ptr(C),
+                                          float(alpha), float(beta), float(gamma), int(sym)),
+                    "sxl_gemm_f64")
+        return C
+
     def set_derived_host(self, F, Kf):
         self._check(self.lib.sxl_set_derived_host(self.h, _host_ptr(F), _host_ptr(Kf)),
                     "sxl_set_derived_host")
@@ -469,7 +489,8 @@ class _BatchContext(Context):
         self.lib = batch.lib
         self.nat = int(n_atoms)
         self.N = 9 * self.nat
-        self.n2 = 2 * self.nat
+        # extended-vector length: per atom, or per (atom, shell) when l-resolved
+        self.n2 = 2 * self.nat * (3 if getattr(mp, "l_resolved", False) else 1)
         self.kmax = int(mp.kmax)
         self.params = make_params(mp, n_atoms, cell, precision)
         self.stream = torch.cuda.current_stream()

@@ -136,3 +136,24 @@ def test_xlbomd_trajectory_matches_oracle(lib):
         assert abs(mu - st_o["mu"]) < 1e-9
         assert abs(st[1] - st_o["T"]) < 1e-6
         assert abs(st[2] - st_o["rms"]) < 1e-9
+
+
+@pytest.mark.parametrize("sym", [False, True])
+def test_gemm_f64_against_numpy(lib, sym):
+    """The fp64 form's product (k_gemm_f64, 64 x 64 tiles) on the 16-atom
+    size N = 144 (two full tiles and a ragged one), with the epilogue
+    alpha A B^T + beta E + gamma I; symmetric mode mirrors the upper tiles."""
+    w = wl.fe16()
+    ctx = _ctx(lib, w)
+    n = w.n_orb
+    rng = np.random.default_rng(8)
+    A = rng.normal(size=(2, n, n))
+    B = A.copy() if sym else rng.normal(size=(2, n, n))
+    E = rng.normal(size=(2, n, n))
+    E = E + np.transpose(E, (0, 2, 1))
+    C = ctx.gemm_f64(A, B, E, alpha=0.7, beta=-1.5, gamma=2.0, sym=sym).cpu().numpy()
+    ref = 0.7 * np.einsum("bij,bkj->bik", A, B) - 1.5 * E + 2.0 * np.eye(n)
+    assert np.abs(C - ref).max() < 1e-12 * np.abs(ref).max()
+    if sym:
+        assert np.array_equal(C, np.transpose(C, (0, 2, 1)))
+    ctx.close()

@@ -1,7 +1,8 @@
 """Parity at the benchmark's size and configuration: the 1024-atom cell
 (9216 orbitals x 2 spins) in both mixed forms (fp16 as bench.py runs it, and
 bf16), against the FP64 oracle (dense eigendecomposition) at the neutral
-start n = 0 of the benchmark's SCF: charges and spins (1e-4 e), one response
+start n = 0 of the benchmark's SCF and at the ferromagnetic start (m_I = 2 +- 0.1):
+charges and spins (1e-4 e), one response
 direction (relative bound n_r * 3 * 2^-12 for fp16, 2^-9 for bf16: the
 response products round their operands to the 16-bit hi parts), the forces
 (1e-3 eV/A) and the energies."""
@@ -23,10 +24,12 @@ def sxl():
     return s
 
 
-@pytest.fixture(scope="module")
-def oracle1024():
+@pytest.fixture(scope="module", params=["neutral", "ferromagnetic"])
+def oracle1024(request):
+    """The oracle at the benchmark's SCF start n = 0 and at the workload's
+    ferromagnetic start (spins m_I = 2 +- 0.1), where q and m differ."""
     w = wl.fe1024()
-    n0 = np.zeros(2 * w.n_atoms)
+    n0 = np.zeros(2 * w.n_atoms) if request.param == "neutral" else w.n0
     d = electronic.density(w.R, w.cell, n0, w.params)
     v = wl.random_direction(w.n_atoms, 21)
     qv_o, _ = d.response(v)
