@@ -272,6 +272,28 @@ int sxl_batch_destroy(sxl_batch* batch);
 int sxl_mixed_gemm(sxl_ctx* ctx, const double* A_dev, const double* B_dev, const double* E_dev,
                    double* C_dev, double alpha, double beta, double gamma, int sym, int split);
 
+/* Tile autotuner of the tensor-core GEMM for one mixed-precision context
+ * (no counterpart in the paper; the tile shapes of the batched form).  Times
+ * every candidate tile of the three product forms on the context's own
+ * chain buffers with CUDA events (3 launches each, after a warm-up): plain
+ * products over K blocks of 64 or 32 and 256- or 128-row tiles, split
+ * products over K blocks of 32 or 64, dual products over 256- or 128-row
+ * tiles; keeps the fastest for this context.  out7_host (may be NULL)
+ * receives [plain K block, plain rows/128, plain ms, split K block, split ms,
+ * dual rows/128, dual ms].  Discards any density the context held.
+ * SXL_E_STATE for an fp64 context. */
+int sxl_autotune(sxl_ctx* ctx, double* out7_host);
+/* Sets the tile choices directly (0 = library default): plain K block 32 or
+ * 64, plain rows per CTA 1 or 2 (x 128), split K block 32 or 64, dual rows
+ * per CTA 1 or 2.  SXL_E_ARG for other values. */
+int sxl_set_tiles(sxl_ctx* ctx, int bk_plain, int mt_plain, int bk_split, int mt_dual);
+/* Autotunes every replica of a batch; replicas with the same chain
+ * dimension share one tuning run.  report_host (may be NULL, 8 doubles per
+ * distinct dimension) receives [chain dimension, the 7 values of
+ * sxl_autotune].  Returns the number of distinct dimensions tuned (>= 1), or
+ * a negative SXL_E_* code. */
+int sxl_batch_autotune(sxl_batch* batch, double* report_host);
+
 /* Diagnostic: the same product in fp64, C[b] = alpha A[b] B[b]^T + beta E[b]
  * + gamma I (b = 0, 1; N x N device arrays, E may be NULL), through the
  * library's fp64 GEMM, the product of every step of the SXL_FP64 chains.

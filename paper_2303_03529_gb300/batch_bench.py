@@ -4,7 +4,7 @@ rank 6), all stepped together by sxl_batch_step, against the same replicas
 stepped one after another (one host thread).  Every replica starts from the
 neutral non-magnetic n = 0 history.
 
-    python -m paper_2303_03529_gb300.batch_bench [--steps K] [--warmup W] [--threads T]
+    python -m paper_2303_03529_gb300.batch_bench [--steps K] [--warmup W] [--threads T] [--autotune]
 
 Prints one JSON line: replica MD steps/s and atom-steps/s of the batch, the
 sequential value, and the tensor-core throughput summed over the replicas.
@@ -33,9 +33,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--threads", type=int, default=48)
     ap.add_argument("--count", type=int, default=48)
+    ap.add_argument("--autotune", action="store_true",
+                    help="tile autotuning of every replica before the run")
     args = ap.parse_args()
     reps = workload.replica_set(args.count)
     b = sxl.Batch(reps, "fp16")
+    tuned = b.autotune() if args.autotune else None
     for ctx, w in zip(b.contexts, reps):
         nat = w.R.shape[0]
         ctx.set_state(w.R, w.V, np.zeros((w.params.kmax + 1, 2 * nat)), float("nan"))
@@ -63,6 +66,9 @@ def main():
         "tensor_tflops_aggregate": round(alg / t_batch / 1e12, 1),
         "gemm_launches": int(sum(t["tc_launches"] for t in tm)),
         "precision": "fp16", "data": "synthetic (workload.replica_set, seeded)",
+        "tiles": "autotuned per chain dimension" if tuned else "library defaults",
+        "tuned": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in t.items()}
+                  for t in tuned] if tuned else None,
     }
     print(json.dumps(out), flush=True)
     b.close()

@@ -533,6 +533,7 @@ int sxl_create(const sxl_params* prm, void* stream, sxl_ctx** out) {
   c->Np = c->N;
   c->dup = nullptr;
   c->tc_err = nullptr;
+  c->tc_bk_plain = c->tc_mt_plain = c->tc_bk_split = c->tc_mt_dual = 0;
   c->diis_N = c->diis_F = c->diis_B = c->diis_coef = nullptr;
   c->diis_list = c->diis_flag = nullptr;
   c->diis_count = c->diis_head = 0;
@@ -977,6 +978,34 @@ int sxl_mixed_gemm(sxl_ctx* c, const double* A, const double* B, const double* E
   int flag = 0;
   SXL_TRY(tc_error_flag(c, &flag));
   if (flag) return sxl_fail(c, SXL_E_CUDA, "tensor-core GEMM reported a wait timeout");
+  return SXL_OK;
+}
+
+int sxl_autotune(sxl_ctx* c, double* out7) {
+  if (!c) return SXL_E_ARG;
+  if (c->p.precision == SXL_FP64) return sxl_fail(c, SXL_E_STATE, "context is fp64");
+  // the timing runs in the chain's buffers: the density is gone
+  c->have_density = false;
+  c->apm_ready = false;
+  c->teff_valid = false;
+  SXL_TRY(mixed_autotune(c, out7));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  int flag = 0;
+  SXL_TRY(tc_error_flag(c, &flag));
+  if (flag) return sxl_fail(c, SXL_E_CUDA, "tensor-core GEMM reported a wait timeout");
+  return SXL_OK;
+}
+
+int sxl_set_tiles(sxl_ctx* c, int bk_plain, int mt_plain, int bk_split, int mt_dual) {
+  if (!c) return SXL_E_ARG;
+  auto ok_bk = [](int b) { return b == 0 || b == 32 || b == 64; };
+  auto ok_mt = [](int m) { return m == 0 || m == 1 || m == 2; };
+  if (!ok_bk(bk_plain) || !ok_mt(mt_plain) || !ok_bk(bk_split) || !ok_mt(mt_dual))
+    return sxl_fail(c, SXL_E_ARG, "tile choice out of range");
+  c->tc_bk_plain = bk_plain;
+  c->tc_mt_plain = mt_plain;
+  c->tc_bk_split = bk_split;
+  c->tc_mt_dual = mt_dual;
   return SXL_OK;
 }
 

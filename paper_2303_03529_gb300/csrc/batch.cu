@@ -7,6 +7,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <array>
 #include <thread>
 
 struct sxl_batch {
@@ -76,6 +77,35 @@ int sxl_batch_step(sxl_batch* b, int nsteps, int nthreads, int* status) {
     if (first == SXL_OK && rc[i] != SXL_OK) first = rc[i];
   }
   return first;
+}
+
+// Tile autotuning of a batch: replicas with the same chain dimension share
+// one tuning run (the first of them is timed, the others take its choice).
+int sxl_batch_autotune(sxl_batch* b, double* report_host) {
+  if (!b) return SXL_E_ARG;
+  std::vector<std::pair<int, std::array<int, 4>>> done;  // (Np, choice)
+  int k = 0;
+  for (size_t i = 0; i < b->ctx.size(); ++i) {
+    sxl_ctx* c = b->ctx[i];
+    bool found = false;
+    for (auto& d : done)
+      if (d.first == c->Np) {
+        SXL_TRY(sxl_set_tiles(c, d.second[0], d.second[1], d.second[2], d.second[3]));
+        found = true;
+        break;
+      }
+    if (found) continue;
+    double out[7];
+    SXL_TRY(sxl_autotune(c, out));
+    done.push_back({c->Np, {(int)out[0], (int)out[1], (int)out[3], (int)out[5]}});
+    if (report_host) {
+      double* r = report_host + 8 * k;
+      r[0] = c->Np;
+      for (int j = 0; j < 7; ++j) r[1 + j] = out[j];
+    }
+    ++k;
+  }
+  return k;  // distinct chain dimensions tuned
 }
 
 int sxl_batch_destroy(sxl_batch* b) {

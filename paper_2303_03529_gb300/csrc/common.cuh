@@ -69,6 +69,9 @@ struct sxl_ctx {
   // bound (empty states)
   int Np;
   int* tc_err;            // the device's tensor-core wait-timeout flag (mixed.cu)
+  // tile choices of the tensor-core GEMM for this context (0: library
+  // default); set by sxl_autotune / sxl_set_tiles
+  int tc_bk_plain, tc_mt_plain, tc_bk_split, tc_mt_dual;
   double* dup;            // 2 x Np perturbation (zero on the padding)
   MatH hU, hS, hQ, hX0, hX1, hP, hSm, hdTa, hdTb, hG1;
   std::vector<MatH> hT, hY;
@@ -247,6 +250,7 @@ void density_matrix_mixed(sxl_ctx* c, double* D);
 int tc_error_flag(sxl_ctx* c, int* flag);
 int mixed_gemm_test(sxl_ctx* c, const double* A, const double* B, const double* E, double* C,
                     double alpha, double beta, double gamma, int sym, int split);
+int mixed_autotune(sxl_ctx* c, double* out7);
 
 // value of element i of a (hi, lo) matrix: hi + lo 2^-LO_SHIFT
 template <bool BF16>

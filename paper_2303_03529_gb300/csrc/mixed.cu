@@ -30,6 +30,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdlib>
+#include <functional>
 #include <mutex>
 
 #define TC_BM 128
@@ -228,19 +229,98 @@ struct TcArgs {
   int kb0 = 0;  // first k block of this launch (a product split over K)
 };
 
+// One 32-column chunk of one accumulator row (the thread's row): C =
+// alpha acc + beta E + gamma I in fp32, stored as (hi, lo); symmetric outputs
+// also store the mirrored element.  a1 is the cross-product accumulator of
+// the split form (unused otherwise).
+template <bool BF16, bool SPLIT>
+__device__ __forceinline__ void epi_chunk(const TcArgs& g, size_t mat, int row, int c0,
+                                          const uint32_t* a0, const uint32_t* a1) {
+  if (row >= g.n || c0 >= g.n) return;  // n % 64 == 0: a chunk is all in or all out
+  const size_t rb = mat + (size_t)row * g.n + c0;
+  float v[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    float x = __uint_as_float(a0[j]);
+    if (SPLIT) x = fmaf(__uint_as_float(a1[j]), LO_INV, x);
+    v[j] = g.alpha * x;
+  }
+  if (g.Ehi) {
+    const uint4* eh = reinterpret_cast<const uint4*>(g.Ehi + rb);
+    const uint4* el = reinterpret_cast<const uint4*>(g.Elo + rb);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      const uint4 h = eh[w], l = el[w];
+      const uint32_t hv[4] = {h.x, h.y, h.z, h.w}, lv[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const uint16_t hb = (uint16_t)(hv[e >> 1] >> (16 * (e & 1)));
+        const uint16_t lb = (uint16_t)(lv[e >> 1] >> (16 * (e & 1)));
+        v[8 * w + e] = fmaf(g.beta, fmaf(HL<BF16>::f(lb), LO_INV, HL<BF16>::f(hb)), v[8 * w + e]);
+      }
+    }
+  }
+  if (row >= c0 && row < c0 + 32) v[row - c0] += g.gamma;
+  // (hi, lo) pairs packed two per 32-bit register (element 2k in the low half)
+  uint32_t hw[16], lw[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const uint16_t h0 = HL<BF16>::b(v[2 * k]), h1 = HL<BF16>::b(v[2 * k + 1]);
+    const uint16_t l0 = HL<BF16>::b((v[2 * k] - HL<BF16>::f(h0)) * LO_SCALE);
+    const uint16_t l1 = HL<BF16>::b((v[2 * k + 1] - HL<BF16>::f(h1)) * LO_SCALE);
+    hw[k] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+    lw[k] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+  }
+  if (!g.sym || row <= c0) {
+    // whole chunk owned: 16-byte stores along the row
+    uint4* oh = reinterpret_cast<uint4*>(g.Chi + rb);
+    uint4* ol = reinterpret_cast<uint4*>(g.Clo + rb);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      oh[w] = make_uint4(hw[4 * w], hw[4 * w + 1], hw[4 * w + 2], hw[4 * w + 3]);
+      ol[w] = make_uint4(lw[4 * w], lw[4 * w + 1], lw[4 * w + 2], lw[4 * w + 3]);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (row <= c0 + j) {
+        g.Chi[rb + j] = (uint16_t)(hw[j >> 1] >> (16 * (j & 1)));
+        g.Clo[rb + j] = (uint16_t)(lw[j >> 1] >> (16 * (j & 1)));
+      }
+  }
+  if (g.sym) {
+    // mirrored element (c, row) for row < c: lanes hold consecutive rows,
+    // so each j writes 32 consecutive elements of row c
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int col = c0 + j;
+      if (row < col) {
+        const size_t mi = mat + (size_t)col * g.n + row;
+        g.Chi[mi] = (uint16_t)(hw[j >> 1] >> (16 * (j & 1)));
+        g.Clo[mi] = (uint16_t)(lw[j >> 1] >> (16 * (j & 1)));
+      }
+    }
+  }
+}
+
 // MT = 2 (plain products only): the CTA covers 256 output rows as two
 // M = 128 MMAs that share each B tile; the second accumulator takes the TMEM
 // columns the split form uses for its cross products.  Per k step the CTA
 // then loads 512 operand rows for 2 x 128 x 256 outputs instead of 384 rows
 // for 128 x 256.
-template <bool SPLIT, int BK, int MT = 1>
+// CPS = 2 (plain products with MT = 1 only): two CTAs share an SM, each with
+// half the operand ring and 256 TMEM columns, so one CTA's epilogue runs
+// while the other's MMAs do.
+template <bool SPLIT, int BK, int MT = 1, int CPS = 1>
 struct TcCfg {
   static_assert(!(SPLIT && MT == 2), "split products use both accumulators");
+  static_assert(CPS == 1 || (!SPLIT && MT == 1), "two CTAs per SM need 256 TMEM columns each");
   static constexpr uint32_t A_BYTES = TC_BM * MT * BK * 2;
   static constexpr uint32_t A_HALF = TC_BM * BK * 2;
   static constexpr uint32_t B_BYTES = TC_BN * BK * 2;
   static constexpr uint32_t STAGE_BYTES = (A_BYTES + B_BYTES) * (SPLIT ? 2 : 1);
-  static constexpr int STAGES = (int)((196608u / STAGE_BYTES) > 8 ? 8 : (196608u / STAGE_BYTES));
+  static constexpr uint32_t RING = 196608u / CPS;
+  static constexpr int STAGES = (int)((RING / STAGE_BYTES) > 8 ? 8 : (RING / STAGE_BYTES));
   static constexpr uint32_t TMEM_COLS = (SPLIT || MT == 2) ? 512 : 256;
   static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 1024;
 };
@@ -248,12 +328,12 @@ struct TcCfg {
 // Dual plain products (DUAL): C = A1 B1^T + A2 B2^T as one product over the
 // concatenated K dimension; the second pair comes in through the tensor maps
 // the split form uses for the lo parts.
-template <bool BF16, bool SPLIT, int BK = TC_BK, int MT = 1, bool DUAL = false>
-__global__ void __launch_bounds__(192, 1)
+template <bool BF16, bool SPLIT, int BK = TC_BK, int MT = 1, bool DUAL = false, int CPS = 1>
+__global__ void __launch_bounds__(192, CPS)
     k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
               TcArgs g) {
-  using Cfg = TcCfg<SPLIT, BK, MT>;
+  using Cfg = TcCfg<SPLIT, BK, MT, CPS>;
   constexpr int STAGES = Cfg::STAGES;
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], acc_bar;
@@ -372,79 +452,21 @@ __global__ void __launch_bounds__(192, 1)
     tc_fence_after();
     if (ok) {
       const size_t mat = (size_t)bz * g.n * g.n;
-      for (int it = 0; it < MT * (TC_BN / 32); ++it) {
-      const int mt = it / (TC_BN / 32);
-      const int cc = (it % (TC_BN / 32)) * 32;
-      const int row = row0 + mt * TC_BM + q * 32 + lane;
-      {
+      constexpr int NIT = MT * (TC_BN / 32);  // 32-column chunks of the tile, in order
+      auto chunk_addr = [&](int it) {
+        return tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((it % (TC_BN / 32)) * 32 +
+                                                               256 * (it / (TC_BN / 32)));
+      };
+      auto chunk_row = [&](int it) { return row0 + (it / (TC_BN / 32)) * TC_BM + q * 32 + lane; };
+      auto chunk_col = [&](int it) { return col0 + (it % (TC_BN / 32)) * 32; };
+#pragma unroll 1
+      for (int it = 0; it < NIT; ++it) {
         uint32_t a0[32], a1[32];
-        const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cc + 256 * mt);
+        const uint32_t ta = chunk_addr(it);
         tmem_ld32(ta, a0);
         if (SPLIT) tmem_ld32(ta + 256, a1);
         tmem_wait_ld();
-        const int c0 = col0 + cc;
-        if (row >= g.n || c0 >= g.n) continue;  // n % 64 == 0: a chunk is all in or all out
-        const size_t rb = mat + (size_t)row * g.n + c0;
-        float v[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          float x = __uint_as_float(a0[j]);
-          if (SPLIT) x = fmaf(__uint_as_float(a1[j]), LO_INV, x);
-          v[j] = g.alpha * x;
-        }
-        if (g.Ehi) {
-          const uint4* eh = reinterpret_cast<const uint4*>(g.Ehi + rb);
-          const uint4* el = reinterpret_cast<const uint4*>(g.Elo + rb);
-#pragma unroll
-          for (int w = 0; w < 4; ++w) {
-            uint4 h = eh[w], l = el[w];
-            const uint16_t* hh = reinterpret_cast<const uint16_t*>(&h);
-            const uint16_t* ll = reinterpret_cast<const uint16_t*>(&l);
-#pragma unroll
-            for (int e = 0; e < 8; ++e)
-              v[8 * w + e] = fmaf(g.beta, fmaf(HL<BF16>::f(ll[e]), LO_INV, HL<BF16>::f(hh[e])),
-                                  v[8 * w + e]);
-          }
-        }
-        if (row >= c0 && row < c0 + 32) v[row - c0] += g.gamma;
-        uint16_t hs[32], ls[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          uint16_t h = HL<BF16>::b(v[j]);
-          hs[j] = h;
-          ls[j] = HL<BF16>::b((v[j] - HL<BF16>::f(h)) * LO_SCALE);
-        }
-        if (!g.sym || row <= c0) {
-          // whole chunk owned: 16-byte stores along the row
-          uint4* oh = reinterpret_cast<uint4*>(g.Chi + rb);
-          uint4* ol = reinterpret_cast<uint4*>(g.Clo + rb);
-#pragma unroll
-          for (int w = 0; w < 4; ++w) {
-            oh[w] = *reinterpret_cast<const uint4*>(&hs[8 * w]);
-            ol[w] = *reinterpret_cast<const uint4*>(&ls[8 * w]);
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; ++j)
-            if (row <= c0 + j) {
-              g.Chi[rb + j] = hs[j];
-              g.Clo[rb + j] = ls[j];
-            }
-        }
-        if (g.sym) {
-          // mirrored element (c, row) for row < c: lanes hold consecutive rows,
-          // so each j writes 32 consecutive elements of row c
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int col = c0 + j;
-            if (row < col) {
-              const size_t mi = mat + (size_t)col * g.n + row;
-              g.Chi[mi] = hs[j];
-              g.Clo[mi] = ls[j];
-            }
-          }
-        }
-      }
+        epi_chunk<BF16, SPLIT>(g, mat, chunk_row(it), chunk_col(it), a0, a1);
       }
     }
   }
@@ -506,14 +528,14 @@ static int make_map(sxl_ctx* c, CUtensorMap* m, const uint16_t* base, int n, int
   return SXL_OK;
 }
 
-template <bool BF16, bool SPLIT, int BK, int MT = 1, bool DUAL = false>
+template <bool BF16, bool SPLIT, int BK, int MT = 1, bool DUAL = false, int CPS = 1>
 static int launch_tc(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a) {
-  using Cfg = TcCfg<SPLIT, BK, MT>;
+  using Cfg = TcCfg<SPLIT, BK, MT, CPS>;
   // set once per instantiation (contexts may launch from several host threads;
   // a repeated set is harmless)
   static std::atomic<bool> attr{false};
   if (!attr.load()) {
-    CUDA_TRY(c, cudaFuncSetAttribute(k_tc_gemm<BF16, SPLIT, BK, MT, DUAL>,
+    CUDA_TRY(c, cudaFuncSetAttribute(k_tc_gemm<BF16, SPLIT, BK, MT, DUAL, CPS>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM));
     attr.store(true);
   }
@@ -524,8 +546,8 @@ static int launch_tc(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a) {
     e1 = ev_get(c);
     CUDA_TRY(c, cudaEventRecord(e0, c->st));
   }
-  k_tc_gemm<BF16, SPLIT, BK, MT, DUAL><<<grid, 192, Cfg::SMEM, c->st>>>(maps[0], maps[1], maps[2],
-                                                                      maps[3], a);
+  k_tc_gemm<BF16, SPLIT, BK, MT, DUAL, CPS><<<grid, 192, Cfg::SMEM, c->st>>>(maps[0], maps[1],
+                                                                           maps[2], maps[3], a);
   ++g_sxl_launches;
   if (c->time_tc) {
     CUDA_TRY(c, cudaEventRecord(e1, c->st));
@@ -549,6 +571,16 @@ static int launch_tc(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a) {
 // K-block per product form (measured at n = 9216): split products run best
 // with 32-wide blocks (four 48 KB stages), plain ones with 64-wide blocks
 // (four 48 KB stages as well).  SXL_TC_BK=32 or 64 forces one width.
+// Plain and dual products on 128-row tiles with two CTAs per SM
+// (SXL_TC_CPS=2) instead of one CTA per 256 x 256 tile (default).
+static int tc_cps() {
+  static const int v = [] {
+    const char* e = getenv("SXL_TC_CPS");
+    return (e && atoi(e) == 2) ? 2 : 1;
+  }();
+  return v;
+}
+
 static int tc_bk(bool split) {
   static const int bk_env = [] {
     const char* e = getenv("SXL_TC_BK");
@@ -563,14 +595,18 @@ static int gemm_tc_range(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C
                          int nkb) {
   const bool bf16 = c->p.precision == SXL_MIXED_BF16;
   const int n = c->Np;
-  const int bk = tc_bk(split);
+  // per-context choices (sxl_autotune) before the library defaults
+  const int bk_ctx = split ? c->tc_bk_split : c->tc_bk_plain;
+  const int bk = bk_ctx ? bk_ctx : tc_bk(split);
   // plain products cover 256 rows per CTA (two M = 128 MMAs per B tile);
   // SXL_TC_MT=1 restores 128-row tiles
   static const int mt_env = [] {
     const char* e = getenv("SXL_TC_MT");
     return e ? atoi(e) : 0;
   }();
-  const int mt = split ? 1 : (mt_env == 1 ? 1 : 2);
+  const int cps = split ? 1 : tc_cps();
+  int mt = split ? 1 : ((mt_env == 1 || cps == 2) ? 1 : 2);
+  if (!split && c->tc_mt_plain && cps == 1) mt = c->tc_mt_plain;
   CUtensorMap maps[4];
   SXL_TRY(make_map(c, &maps[0], A.hi, n, TC_BM * mt, bf16, bk));
   SXL_TRY(make_map(c, &maps[1], A.lo, n, TC_BM * mt, bf16, bk));
@@ -596,6 +632,12 @@ static int gemm_tc_range(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C
   if (split) {
     if (bk == 64) return bf16 ? launch_tc<true, true, 64>(c, maps, a) : launch_tc<false, true, 64>(c, maps, a);
     return bf16 ? launch_tc<true, true, 32>(c, maps, a) : launch_tc<false, true, 32>(c, maps, a);
+  }
+  if (cps == 2) {
+    if (bk == 64) return bf16 ? launch_tc<true, false, 64, 1, false, 2>(c, maps, a)
+                              : launch_tc<false, false, 64, 1, false, 2>(c, maps, a);
+    return bf16 ? launch_tc<true, false, 32, 1, false, 2>(c, maps, a)
+                : launch_tc<false, false, 32, 1, false, 2>(c, maps, a);
   }
   if (mt == 2) {
     if (bk == 64) return bf16 ? launch_tc<true, false, 64, 2>(c, maps, a) : launch_tc<false, false, 64, 2>(c, maps, a);
@@ -643,7 +685,9 @@ int gemm_tc_k(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C, float alp
 int gemm_tc_dual(sxl_ctx* c, const MatH& A1, const MatH& B1, const MatH& A2, const MatH& B2,
                  const MatH& C, float alpha, const MatH* E, float beta, float gamma, bool sym) {
   const bool bf16 = c->p.precision == SXL_MIXED_BF16;
-  const int n = c->Np, bk = 64, mt = 2;
+  const int cps = tc_cps();
+  const int n = c->Np, bk = 64;
+  const int mt = cps == 2 ? 1 : (c->tc_mt_dual ? c->tc_mt_dual : 2);
   CUtensorMap maps[4];
   SXL_TRY(make_map(c, &maps[0], A1.hi, n, TC_BM * mt, bf16, bk));
   SXL_TRY(make_map(c, &maps[1], A2.hi, n, TC_BM * mt, bf16, bk));
@@ -665,8 +709,101 @@ int gemm_tc_dual(sxl_ctx* c, const MatH& A1, const MatH& B1, const MatH& A2, con
   a.sym = sym ? 1 : 0;
   a.err = c->tc_err;
   c->n_gemm++;
+  if (cps == 2)
+    return bf16 ? launch_tc<true, false, 64, 1, true, 2>(c, maps, a)
+                : launch_tc<false, false, 64, 1, true, 2>(c, maps, a);
+  if (mt == 1)
+    return bf16 ? launch_tc<true, false, 64, 1, true>(c, maps, a)
+                : launch_tc<false, false, 64, 1, true>(c, maps, a);
   return bf16 ? launch_tc<true, false, 64, 2, true>(c, maps, a)
               : launch_tc<false, false, 64, 2, true>(c, maps, a);
+}
+
+// ---------------------------------------------------------------------------
+// Tile autotuner (per context): every candidate tile of the plain, dual and
+// split products is timed with CUDA events on the context's own chain
+// buffers (filled with a fixed pattern) and the fastest is kept.  Small
+// chains (few output tiles per launch) favour 128-row tiles, which double the
+// CTAs; large ones the 256-row tiles that halve the operand traffic.
+__global__ void k_fill_pattern(size_t nn, uint16_t* hi, uint16_t* lo, int bf16) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  uint32_t h = (uint32_t)(i * 2654435761u);
+  const float v = ((h >> 8) & 0xffff) * (1.0f / 65536.0f) - 0.5f;
+  if (bf16) {
+    hi[i] = __bfloat16_as_ushort(__float2bfloat16_rn(v * 0.01f));
+    lo[i] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+  } else {
+    hi[i] = __half_as_ushort(__float2half_rn(v * 0.01f));
+    lo[i] = __half_as_ushort(__float2half_rn(v));
+  }
+}
+
+static int time_launches(sxl_ctx* c, const std::function<int()>& fn, int reps, float* ms) {
+  SXL_TRY(fn());  // warm-up (and the kernel attributes)
+  cudaEvent_t e0, e1;
+  CUDA_TRY(c, cudaEventCreate(&e0));
+  CUDA_TRY(c, cudaEventCreate(&e1));
+  CUDA_TRY(c, cudaEventRecord(e0, c->st));
+  for (int r = 0; r < reps; ++r) SXL_TRY(fn());
+  CUDA_TRY(c, cudaEventRecord(e1, c->st));
+  CUDA_TRY(c, cudaEventSynchronize(e1));
+  float t = 0.f;
+  CUDA_TRY(c, cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms = t / reps;
+  return SXL_OK;
+}
+
+int mixed_autotune(sxl_ctx* c, double* out) {
+  const size_t nn = 2 * (size_t)c->Np * c->Np;
+  const int bf16 = c->p.precision == SXL_MIXED_BF16;
+  LAUNCH(k_fill_pattern, (unsigned)((nn + 255) / 256), 256, 0, c->st, nn, c->hU.hi, c->hU.lo, bf16);
+  LAUNCH(k_fill_pattern, (unsigned)((nn + 255) / 256), 256, 0, c->st, nn, c->hS.hi, c->hS.lo, bf16);
+  const int reps = 3;
+  // plain: (K block, rows per CTA)
+  const int pc[4][2] = {{64, 2}, {64, 1}, {32, 2}, {32, 1}};
+  float best = 1e30f;
+  int bi = 0;
+  for (int i = 0; i < 4; ++i) {
+    c->tc_bk_plain = pc[i][0];
+    c->tc_mt_plain = pc[i][1];
+    float ms = 0.f;
+    SXL_TRY(time_launches(c, [&] { return gemm_tc(c, c->hU, c->hS, c->hG1, 1.f, nullptr, 0.f, 0.f,
+                                                  false, false); }, reps, &ms));
+    if (ms < best) { best = ms; bi = i; }
+  }
+  c->tc_bk_plain = pc[bi][0];
+  c->tc_mt_plain = pc[bi][1];
+  if (out) { out[0] = pc[bi][0]; out[1] = pc[bi][1]; out[2] = best; }
+  // split: K block
+  const int sc[2] = {32, 64};
+  best = 1e30f;
+  bi = 0;
+  for (int i = 0; i < 2; ++i) {
+    c->tc_bk_split = sc[i];
+    float ms = 0.f;
+    SXL_TRY(time_launches(c, [&] { return gemm_tc(c, c->hU, c->hS, c->hG1, 1.f, nullptr, 0.f, 0.f,
+                                                  true, true); }, reps, &ms));
+    if (ms < best) { best = ms; bi = i; }
+  }
+  c->tc_bk_split = sc[bi];
+  if (out) { out[3] = sc[bi]; out[4] = best; }
+  // dual: rows per CTA
+  const int dc[2] = {2, 1};
+  best = 1e30f;
+  bi = 0;
+  for (int i = 0; i < 2; ++i) {
+    c->tc_mt_dual = dc[i];
+    float ms = 0.f;
+    SXL_TRY(time_launches(c, [&] { return gemm_tc_dual(c, c->hU, c->hS, c->hS, c->hU, c->hG1, 1.f,
+                                                       nullptr, 0.f, 0.f, true); }, reps, &ms));
+    if (ms < best) { best = ms; bi = i; }
+  }
+  c->tc_mt_dual = dc[bi];
+  if (out) { out[5] = dc[bi]; out[6] = best; }
+  return SXL_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1150,25 +1287,30 @@ int foe_mixed(sxl_ctx* c, double mu, double* stats_dev) {
 const MatH& final_T_mixed(const sxl_ctx* c) { return c->teff_valid ? c->hTeff : c->hT[c->nr]; }
 
 // Shift of the chemical potential by dmu without rerunning the expansion,
-// to second order in s = beta dmu / 2: with t = tanh(y) and y -> y - s,
-//   tanh(y - s) = t - s (1 - t^2) - s^2 t (1 - t^2) + O(s^3)
-// (the perturbation commutes with H), so
-//   T_eff = (1 - s^2) T - s I + T (s T + s^2 T^2),
-// one product for T^2 and one for T (s T + s^2 T^2) with the rest in its
-// epilogue.  The neglected term is at most s^3 / 3 in T (4e-5 at s = 0.05).
+// to third order in s = beta dmu / 2: with t = tanh(y) and y -> y - s,
+//   tanh(y - s) = t - s (1 - t^2) - s^2 t (1 - t^2)
+//                 + s^3 (1 - t^2)(1 - 3 t^2) / 3 + O(s^4)
+// (the perturbation commutes with H), i.e. with P = T^2
+//   T_eff = c0 I + c1 T + c2 P + P (s^2 T + s^3 P),
+//   c0 = -s + s^3/3, c1 = 1 - s^2, c2 = s - 4 s^3/3:
+// one product for P and one for P (s^2 T + s^3 P), the rest in its epilogue
+// (E = c1 T + c2 P).  The neglected term is O(s^4) (2e-6 in T at s = 0.05).
 // The response chain keeps T_nr.
 int mu_shift_mixed(sxl_ctx* c, double dmu, double* stats_dev) {
   const int N = c->N;
   const double sd = 0.5 * c->beta * dmu;
+  const double s2 = sd * sd, s3 = s2 * sd;
   const MatH& T = c->hT[c->nr];
-  SXL_TRY(gemm_tc(c, T, T, c->hSm, 1.f, nullptr, 0.f, 0.f, true, true));       // T^2
+  SXL_TRY(gemm_tc(c, T, T, c->hSm, 1.f, nullptr, 0.f, 0.f, true, true));       // P = T^2
   // Tr T^3 = <T, T^2> per spin for the entropy's shift correction
   DISPATCH(c, k_dot_block_partial, dim3(64, 2), 256, 0, N, c->Np, T.hi, T.lo, c->hSm.hi,
            c->hSm.lo, c->red + 2048);
   LAUNCH(k_sum_parts, 1, 256, 0, c->st, 64, c->red + 2048, c->red + MU_SHIFT_TRACES + 4);
   LAUNCH(k_sum_parts, 1, 256, 0, c->st, 64, c->red + 2048 + 64, c->red + MU_SHIFT_TRACES + 5);
-  symcombo_h(c, c->hP, sd * sd, &c->hSm, 0.5 * sd, &T, 0.0, nullptr, nullptr);  // s T + s^2 T^2
-  SXL_TRY(gemm_tc(c, T, c->hP, c->hTeff, 1.f, &T, (float)(1.0 - sd * sd), (float)(-sd), true,
+  symcombo_h(c, c->hP, s3, &c->hSm, 0.5 * s2, &T, 0.0, nullptr, nullptr);        // s^2 T + s^3 P
+  symcombo_h(c, c->hX1, 1.0 - s2, &T, 0.5 * (sd - 4.0 * s3 / 3.0), &c->hSm, 0.0, nullptr,
+             nullptr);                                                            // c1 T + c2 P
+  SXL_TRY(gemm_tc(c, c->hSm, c->hP, c->hTeff, 1.f, &c->hX1, 1.f, (float)(-sd + s3 / 3.0), true,
                   true));
   c->teff_valid = true;
   c->fo_h = 0.5 * c->beta * dmu;

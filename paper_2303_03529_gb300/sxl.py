@@ -88,6 +88,9 @@ EXPORTS = {
     "sxl_enable_gemm_timing": (_i, [_p, _i]),
     "sxl_gemm_timers": (_i, [_p, _p, _i]),
     "sxl_gemm_f64": (_i, [_p, _p, _p, _p, _p, _d, _d, _d, _i]),
+    "sxl_autotune": (_i, [_p, _p]),
+    "sxl_set_tiles": (_i, [_p, _i, _i, _i, _i]),
+    "sxl_batch_autotune": (_i, [_p, _p]),
     "sxl_mixed_gemm_noalloc": (_i, [_i, _i, _p, _p, _p, _p, _d, _d, _d, _i, _i, _p]),
 }
 
@@ -354,6 +357,19 @@ class Context:
                                             int(split)), "sxl_mixed_gemm")
         return C
 
+    def autotune(self):
+        """Times the candidate tensor-core tiles on this context and keeps the
+        fastest; returns the choice and the times (ms)."""
+        out = np.zeros(7)
+        self._check(self.lib.sxl_autotune(self.h, out.ctypes.data_as(_p)), "sxl_autotune")
+        return {"plain_bk": int(out[0]), "plain_rows": 128 * int(out[1]), "plain_ms": out[2],
+                "split_bk": int(out[3]), "split_ms": out[4], "dual_rows": 128 * int(out[5]),
+                "dual_ms": out[6]}
+
+    def set_tiles(self, bk_plain=0, mt_plain=0, bk_split=0, mt_dual=0):
+        self._check(self.lib.sxl_set_tiles(self.h, int(bk_plain), int(mt_plain), int(bk_split),
+                                           int(mt_dual)), "sxl_set_tiles")
+
     def gemm_f64(self, A, B, E=None, alpha=1.0, beta=0.0, gamma=0.0, sym=False):
         """C = alpha A B^T + beta E + gamma I in fp64 (2 x N x N), the fp64
         form's product."""
@@ -533,6 +549,17 @@ class Batch:
             if self.lib.sxl_batch_context(self.h, i, ctypes.byref(c)) != 0:
                 raise SxlError("sxl_batch_context failed")
             self.contexts.append(_BatchContext(self, c, w.params, w.R.shape[0], w.cell, precision))
+
+    def autotune(self):
+        """Tile autotuning of every replica (one run per distinct chain
+        dimension); returns one dict per tuned dimension."""
+        rep = np.zeros((len(self.contexts), 8))
+        k = self.lib.sxl_batch_autotune(self.h, rep.ctypes.data_as(_p))
+        if k < 0:
+            raise SxlError(f"sxl_batch_autotune failed ({k})")
+        keys = ("n", "plain_bk", "plain_mt", "plain_ms", "split_bk", "split_ms", "dual_mt",
+                "dual_ms")
+        return [dict(zip(keys, r.tolist())) for r in rep[:k]]
 
     def step(self, nsteps=1, nthreads=0):
         """nsteps sXL-BOMD steps of every replica; returns the per-replica

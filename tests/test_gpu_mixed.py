@@ -148,3 +148,37 @@ def test_mixed_padded_chain(sxl, prec, ncell, vac):
     print(f"padded {nat} {prec}: rel {rel:.2e} |dF| {err_f:.2e} dU/atom {dU:.2e}")
     assert dU < (1e-3 if prec == "fp16" else 5e-3)
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_every_tile_choice_gives_the_product(sxl, prec):
+    """Every tile the autotuner may pick (plain: K block 64/32 x 256/128-row
+    tiles; split: K block 32/64; dual: 256/128-row tiles) computes the same
+    product within the form's bound at N = 1152 (ragged 256-column edge), and
+    the autotuner returns one of them."""
+    w = wl.fe128()
+    ctx = sxl.Context(w.params, w.n_atoms, w.cell, prec)
+    n = w.n_orb
+    rng = np.random.default_rng(3)
+    A = np.stack([_sym(rng, n), _sym(rng, n)])
+    B = np.stack([_sym(rng, n), _sym(rng, n)])
+    ref = np.einsum("bij,bkj->bik", A, B)
+    ref_dual = ref + np.einsum("bij,bkj->bik", B, A)
+    eps_hi = 2.0 ** -11 if prec == "fp16" else 2.0 ** -8
+    eps_split = max(2.0 ** -22 if prec == "fp16" else 2.0 ** -16, 2.0 ** -21)
+    for bk in (64, 32):
+        for mt in (2, 1):
+            ctx.set_tiles(bk_plain=bk, mt_plain=mt, bk_split=bk, mt_dual=mt)
+            C = ctx.mixed_gemm(A, B, split=False).cpu().numpy()
+            assert np.abs(C - ref).max() / np.abs(ref).max() < 20 * eps_hi, (bk, mt)
+            C = ctx.mixed_gemm(A, B, split=True).cpu().numpy()
+            assert np.abs(C - ref).max() / np.abs(ref).max() < 20 * eps_split, (bk, mt)
+            C = ctx.mixed_gemm(A, B, sym=True, split=2).cpu().numpy()
+            assert np.abs(C - ref_dual).max() / np.abs(ref_dual).max() < 40 * eps_hi, (bk, mt)
+    t = ctx.autotune()
+    print(f"{prec} autotune at N = {n}: {t}")
+    assert t["plain_bk"] in (32, 64) and t["plain_rows"] in (128, 256)
+    assert t["split_bk"] in (32, 64) and t["dual_rows"] in (128, 256)
+    with pytest.raises(sxl.SxlError):
+        ctx.set_tiles(bk_plain=48)
+    ctx.close()
