@@ -251,7 +251,18 @@ def fe54_general() -> Workload:
     return w
 
 
-WORKLOADS = {"fe16": fe16, "fe128": fe128, "fe1024": fe1024, "fe2000": fe2000}
+def fe128_general() -> Workload:
+    """The 128-atom cell of the general model (overlap, shells resolved)."""
+    w = fe128()
+    w.params = general_model(w.params)
+    w.n0 = shell_resolved_n(w.n0)
+    w.name = "fe128_bcc4x4x4_general"
+    return w
+
+
+WORKLOADS = {"fe16": fe16, "fe128": fe128, "fe1024": fe1024, "fe2000": fe2000,
+             "fe16_general": fe16_general, "fe54_general": fe54_general,
+             "fe128_general": fe128_general}
 
 
 def random_direction(n_atoms: int, seed: int) -> np.ndarray:
