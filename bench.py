@@ -206,14 +206,21 @@ def replica_throughput(steps_per_rank: int, world: int, max_seconds: float) -> f
 
 def prepare_state(sxl, w, precision, local):
     """Initial MD state: SCF from n = 0 with the Krylov kernel mixer and
-    K0 = -I (outside the timed region), all history slots = n*."""
+    K0 = -I (outside the timed region), all history slots = n*.  The general
+    model's mixer starts at the first iteration (its linear-mixing phase
+    would take ~40 iterations; from n = 0 the kernel mixer converges in 5)."""
     import numpy as np
     import torch
     p = w.params
+    general = bool(getattr(p, "l_resolved", False))
     ctx = sxl.Context(p, w.n_atoms, w.cell, precision, scf_keep_k0=1)
     n0 = np.zeros(ctx.n2)
     t0 = time.time()
-    n_star, iters, rms = ctx.scf(w.R, n0, tol=1e-5, max_iter=40)
+    if general:
+        n_star, iters, rms, _ = ctx.scf_ex(w.R, n0, tol=1e-5, max_iter=40, mixer="kernel",
+                                           switch_rms=1.0)
+    else:
+        n_star, iters, rms = ctx.scf(w.R, n0, tol=1e-5, max_iter=40)
     t_scf = time.time() - t0
     _, mu = ctx.density(w.R, n_star)
     nh = torch.stack([n_star] * (p.kmax + 1)).contiguous()

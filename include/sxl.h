@@ -93,8 +93,11 @@ typedef struct {
                                 SXL_FP64, 1e-6 N_e for the mixed forms)      */
   int    scf_keep_k0;        /* scf_solve: 0 = build the exact K0 = J^{-1} when the
                                 kernel mixer starts, 1 = keep the installed K0 */
-  /* Paper-general model (Sec. II.C, Sec. III.A); SXL_FP64 only.  All S0 = 0
-   * and l_resolved = 0 give the orthogonal per-atom model above.          */
+  /* Paper-general model (Sec. II.C, Sec. III.A), every precision.  All S0 = 0
+   * and l_resolved = 0 give the orthogonal per-atom model above.  The mixed
+   * forms hold Z and S^{1/2} in fp16 (hi, lo) pairs (the bf16 form too),
+   * build Z (H - mu0 S) Z about a reference mu0 near mu, and rescale D and
+   * the energy-weighted W to the traces Z S Z = I fixes.                  */
   double S0[10];             /* overlap integrals, same order as V0: S_ii = 1,
                                 S between atoms = Slater-Koster blocks of
                                 S0 exp(-s_decay (r - r0)) s(r); D = Z f(Z^T H Z) Z^T

@@ -207,13 +207,15 @@ static int build_model(sxl_ctx* c, const double* R, const double* n) {
   if (!c->h0_valid || std::memcmp(hR.data(), hC.data(), hR.size() * sizeof(double)) != 0) {
     launch_build_h0(c, R);
     launch_build_gamma(c, R);
-    if (c->general) SXL_TRY(general_overlap(c, R));
+    if (c->general)
+      SXL_TRY(c->p.precision == SXL_FP64 ? general_overlap(c, R) : general_overlap_mixed(c, R));
     CUDA_TRY(c, cudaMemcpyAsync(c->Rcur, R, 3 * c->nat * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     c->h0_valid = true;
   }
   if (c->general) {
     // H_perp = Z H Z and its Gershgorin bounds
-    SXL_TRY(general_hamiltonian(c, n, c->red));
+    SXL_TRY(c->p.precision == SXL_FP64 ? general_hamiltonian(c, n, c->red)
+                                       : general_hamiltonian_mixed(c, n, c->red));
   } else {
     launch_spin_shift(c, n, c->shift);
     lanczos_bounds(c, c->red);
@@ -226,7 +228,9 @@ static int build_model(sxl_ctx* c, const double* R, const double* n) {
   return SXL_OK;
 }
 
-static int density(sxl_ctx* c, const double* R, const double* n, double mu_guess) {
+// One build of the model at (R, n) and the search for mu (no finishing).
+static int density_pass(sxl_ctx* c, const double* R, const double* n, double mu_guess,
+                        double* mu_out) {
   SXL_TRY(build_model(c, R, n));
   const double Ne = c->p.n_elec_per_atom * c->nat;
   const double kT = c->p.kT;
@@ -317,7 +321,29 @@ static int density(sxl_ctx* c, const double* R, const double* n, double mu_guess
     if (!(mn > lo && mn < hi)) mn = 0.5 * (lo + hi);
     mu = mn;
   }
-  if (c->general) SXL_TRY(general_finish_density(c));
+  *mu_out = mu;
+  return SXL_OK;
+}
+
+// The density at (R, n).  The general model's mixed forms build the
+// orthogonalized Hamiltonian about a reference mu0 (general_mixed.cu): the
+// best estimate of mu before the search (the guess, else the last mu), and
+// when the search ends farther than kT/2 from it, once more about the mu
+// found (Z cached, so only the two products of H_perp and a search pass
+// from a bracketing start).
+static int density(sxl_ctx* c, const double* R, const double* n, double mu_guess) {
+  const bool mixed = c->p.precision != SXL_FP64;
+  const bool about_mu0 = c->general && mixed;
+  if (about_mu0) c->mu0 = std::isfinite(mu_guess) ? mu_guess : c->mu;
+  double mu = 0.0;
+  for (int pass = 0;; ++pass) {
+    SXL_TRY(density_pass(c, R, n, mu_guess, &mu));
+    if (!about_mu0 || pass > 0 || std::fabs(mu - c->mu0) <= 0.5 * c->p.kT) break;
+    c->mu0 = mu;
+    mu_guess = mu;
+  }
+  if (c->general)
+    SXL_TRY(mixed ? general_finish_density_mixed(c) : general_finish_density(c));
   c->mu = mu;
   c->have_density = true;
   return SXL_OK;
@@ -325,7 +351,9 @@ static int density(sxl_ctx* c, const double* R, const double* n, double mu_guess
 
 static int response(sxl_ctx* c, const double* v, double* qv, double* dmu_dev) {
   if (!c->have_density) return sxl_fail(c, SXL_E_STATE, "no density: call sxl_density first");
-  if (c->general) return general_response(c, v, qv, dmu_dev);
+  if (c->general)
+    return c->p.precision == SXL_FP64 ? general_response(c, v, qv, dmu_dev)
+                                      : dmpt_mixed_general(c, v, qv, dmu_dev);
   launch_spin_shift(c, v, c->dh);
   perturb_du(c, c->dh, c->du);
   if (c->p.precision != SXL_FP64) SXL_TRY(dmpt_mixed(c, c->du));
@@ -459,7 +487,9 @@ static int entropy_f64(sxl_ctx* c, double* out_dev) {
 // forces at the current density; energies (6 doubles, host) if requested
 static int eval_forces(sxl_ctx* c, const double* R, const double* n, double* F, double* en) {
   double* erep = c->tmpv;  // nat doubles
-  if (c->general) SXL_TRY(general_forces(c, R, n, F, erep));
+  if (c->general)
+    SXL_TRY(c->p.precision == SXL_FP64 ? general_forces(c, R, n, F, erep)
+                                       : general_forces_mixed(c, R, n, F, erep));
   else launch_forces(c, R, n, c->q, F, erep);
   if (en) {
     const size_t nn = (size_t)c->N * c->N;
@@ -523,8 +553,6 @@ int sxl_create(const sxl_params* prm, void* stream, sxl_ctx** out) {
   if (general && !(p.s_decay > 0)) return SXL_E_ARG;
   for (int i = 0; i < 3; ++i)
     if (!std::isfinite(p.J_l[i])) return SXL_E_ARG;
-  // the paper-general model runs in the fp64 form only
-  if (general && p.precision != SXL_FP64) return SXL_E_UNSUPPORTED;
   sxl_ctx* c = new sxl_ctx();
   c->p = p;
   c->st = (cudaStream_t)stream;

@@ -5,6 +5,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 #include <atomic>
+#include <cmath>
 #include <string>
 #include <vector>
 
@@ -72,12 +73,18 @@ struct sxl_ctx {
   // tile choices of the tensor-core GEMM for this context (0: library
   // default); set by sxl_autotune / sxl_set_tiles
   int tc_bk_plain, tc_mt_plain, tc_bk_split, tc_mt_dual;
+  // true while the general model's overlap-side products (those with Z or
+  // S^{1/2}) run: they take fp16 pairs in the bf16 form too (general_mixed.cu)
+  bool pairs_fp16 = false;
+  // general model, mixed forms: H_perp is held as Z (H - mu0 S) Z (NAN: 0)
+  double mu0 = NAN;
   double* dup;            // 2 x Np perturbation (zero on the padding)
   MatH hU, hS, hQ, hX0, hX1, hP, hSm, hdTa, hdTb, hG1;
   std::vector<MatH> hT, hY;
   std::vector<MatH> hAm;  // Y_k - T_{k+1}/2 (response form; hY[k] then holds Y_k + T_{k+1}/2)
   bool apm_ready;         // hY / hAm hold the response operators of the current chain
   MatH hTeff;             // T_nr after a first-order chemical-potential shift
+  MatH hZg, hSh, hHp;     // general model, mixed forms: Z = S^{-1/2}, S^{1/2}, Z H Z
   float* fscratch;        // 2 Np^2 fp32 (entropy factorizations, mixed forms)
   bool teff_valid;        // hTeff (not hT[nr]) holds the final density
   double fo_h;            // h = beta dmu / 2 of the mu shift in hTeff (0: none)
@@ -251,6 +258,44 @@ int tc_error_flag(sxl_ctx* c, int* flag);
 int mixed_gemm_test(sxl_ctx* c, const double* A, const double* B, const double* E, double* C,
                     double alpha, double beta, double gamma, int sym, int split);
 int mixed_autotune(sxl_ctx* c, double* out7);
+// tensor-core products and elementwise helpers of the mixed chains (mixed.cu)
+int gemm_tc(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C, float alpha, const MatH* E,
+            float beta, float gamma, bool sym, bool split);
+int gemm_tc_dual(sxl_ctx* c, const MatH& A1, const MatH& B1, const MatH& A2, const MatH& B2,
+                 const MatH& C, float alpha, const MatH* E, float beta, float gamma, bool sym);
+void symcombo_h(sxl_ctx* c, const MatH& out, double a, const MatH* X, double b, const MatH* Y,
+                double cc, const double* w, const MatH* Z);
+void axpy_diag_h(sxl_ctx* c, const MatH& out, double a, const MatH& X, double g);
+void rowstats_h(sxl_ctx* c, const MatH& T, double* diag, double* rowsq);
+void rowdot_h(sxl_ctx* c, const MatH& A, const MatH& B, double scale, double* out);
+int halloc(sxl_ctx* c, MatH* m);
+void hfree(MatH& m);
+// the 16-bit pair type of the products issued now: bf16 in the bf16 form,
+// except inside the general model's overlap-side products
+inline bool pairs_bf16(const sxl_ctx* c) {
+  return c->p.precision == SXL_MIXED_BF16 && !c->pairs_fp16;
+}
+// out[r] = sum_j A[r][j] B[r][j] over the 2 N rows of two 2 x N x N fp64
+// matrices (general.cu)
+void rowdot_f64(sxl_ctx* c, const double* A, const double* B, double* out);
+// general model in the mixed forms (general_mixed.cu)
+int general_overlap_mixed(sxl_ctx* c, const double* R);
+int general_hamiltonian_mixed(sxl_ctx* c, const double* n, double* out2_dev);
+void build_u_general_h(sxl_ctx* c, double mu, double scale, double e_pad);
+int general_finish_density_mixed(sxl_ctx* c);
+int general_response_start_mixed(sxl_ctx* c, const double* v, const MatH& dA);
+int general_response_end_mixed(sxl_ctx* c, const MatH& dT, double* qv, double* dmu_dev);
+int dmpt_mixed_general(sxl_ctx* c, const double* v, double* qv, double* dmu_dev);
+int general_forces_mixed(sxl_ctx* c, const double* R, const double* n, double* F, double* erep);
+// shared pieces (general.cu)
+int general_overlap_build(sxl_ctx* c, const double* R, double* cs_out);
+void general_hbuild(sxl_ctx* c, const double* H0, const double* v, double* out);
+void minmax_pairs(sxl_ctx* c, int rows, const double* lohi, double* out2);
+void general_potentials(sxl_ctx* c, const double* n, double* vout);
+void general_group_q(sxl_ctx* c);
+void general_response_stats(sxl_ctx* c, double* qv, double* dmu_dev);
+void general_forces_tail(sxl_ctx* c, const double* R, const double* n, const double* W,
+                         double* F, double* erep);
 
 // value of element i of a (hi, lo) matrix: hi + lo 2^-LO_SHIFT
 template <bool BF16>

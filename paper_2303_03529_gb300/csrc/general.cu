@@ -126,7 +126,11 @@ __global__ void k_scale_copy2(size_t nn, double s, const double* __restrict__ A,
 // Z_k -> A^{-1/2} quadratically while the eigenvalues of A lie in (0, 1];
 // stops one iteration after max |Z_k Y_k - I| < 1e-10 (at most 60
 // iterations, else SXL_E_NO_CONVERGENCE), and Z = Z_k / sqrt(c).
-int general_overlap(sxl_ctx* c, const double* R) {
+__global__ void k_hbuild(int N, const double* __restrict__ H0, const double* __restrict__ S,
+                         const double* __restrict__ v, double* __restrict__ out);
+
+// S (fp64, both spin blocks) at positions R and its Gershgorin upper bound
+int general_overlap_build(sxl_ctx* c, const double* R, double* cs_out) {
   const int N = c->N;
   const size_t nn = (size_t)N * N;
   launch_build_overlap(c, R, c->Sb);
@@ -139,8 +143,26 @@ int general_overlap(sxl_ctx* c, const double* R) {
   CUDA_TRY(c, cudaMemcpyAsync(c->hred, c->red + 3300, 2 * sizeof(double), cudaMemcpyDeviceToHost,
                               c->st));
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
-  const double cs = c->hred[1];
-  if (!(cs > 0) || !std::isfinite(cs)) return sxl_fail(c, SXL_E_NAN, "non-finite overlap matrix");
+  *cs_out = c->hred[1];
+  if (!(*cs_out > 0) || !std::isfinite(*cs_out))
+    return sxl_fail(c, SXL_E_NAN, "non-finite overlap matrix");
+  return SXL_OK;
+}
+
+void general_hbuild(sxl_ctx* c, const double* H0, const double* v, double* out) {
+  const size_t nn = (size_t)c->N * c->N;
+  LAUNCH(k_hbuild, (unsigned)((2 * nn + 255) / 256), 256, 0, c->st, c->N, H0, c->Sb, v, out);
+}
+
+void minmax_pairs(sxl_ctx* c, int rows, const double* lohi, double* out2) {
+  LAUNCH(k_minmax_pairs, 1, 256, 0, c->st, rows, lohi, out2);
+}
+
+int general_overlap(sxl_ctx* c, const double* R) {
+  const int N = c->N;
+  const size_t nn = (size_t)N * N;
+  double cs = 0.0;
+  SXL_TRY(general_overlap_build(c, R, &cs));
   // Y alternates between X0 and G1, Z between X1 and U, the products sit in
   // P and Sm (first spin block of each; all free outside a density pass)
   double* const ybuf[2] = {c->X0, c->G1};
@@ -235,17 +257,22 @@ __global__ void k_rowdot_f64(int n, int rows, const double* __restrict__ A,
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   if (lane == 0) out[row] = s;
 }
-static void rowdot_f64(sxl_ctx* c, const double* A, const double* B, double* out) {
+void rowdot_f64(sxl_ctx* c, const double* A, const double* B, double* out) {
   const int wpb = 8, rows = 2 * c->N;
   LAUNCH(k_rowdot_f64, (rows + wpb - 1) / wpb, 32 * wpb, 0, c->st, c->N, rows, A, B, out);
 }
 
+void general_potentials(sxl_ctx* c, const double* n, double* vout) {
+  const int wpb = 8, G = c->G;
+  LAUNCH(k_potentials, (c->nat + wpb - 1) / wpb, 32 * wpb, 0, c->st, c->nat, G, c->gamma_m, n,
+         G == 3 ? c->p.J_l[0] : 0.5 * c->p.W, c->p.J_l[1], c->p.J_l[2], vout);
+}
+
 int general_hamiltonian(sxl_ctx* c, const double* n, double* out2_dev) {
-  const int N = c->N, G = c->G;
+  const int N = c->N;
   const size_t nn = (size_t)N * N;
   const int wpb = 8;
-  LAUNCH(k_potentials, (c->nat + wpb - 1) / wpb, 32 * wpb, 0, c->st, c->nat, G, c->gamma_m, n,
-         G == 3 ? c->p.J_l[0] : 0.5 * c->p.W, c->p.J_l[1], c->p.J_l[2], c->vorb);
+  general_potentials(c, n, c->vorb);
   LAUNCH(k_hbuild, (unsigned)((2 * nn + 255) / 256), 256, 0, c->st, N, c->H0, c->Sb, c->vorb,
          c->Mg);
   gemm_f64(c, 2, N, c->Zb, c->Mg, c->P, 1.0, nullptr, 0.0, 0.0, false);   // Z H
@@ -289,6 +316,11 @@ __global__ void k_group_q(int nat, int G, const double* __restrict__ dsd, double
   }
 }
 
+void general_group_q(sxl_ctx* c) {
+  LAUNCH(k_group_q, (2 * c->nat + 255) / 256, 256, 0, c->st, c->nat, c->G, c->dsd, c->p.d0_s,
+         c->p.d0_p, c->p.d0_d, c->q);
+}
+
 int general_finish_density(sxl_ctx* c) {
   const int N = c->N, nr = c->nr;
   const double* T = c->T[nr];
@@ -297,8 +329,7 @@ int general_finish_density(sxl_ctx* c) {
   gemm_f64(c, 2, N, c->Zb, c->P, c->G1, 1.0, nullptr, 0.0, 0.0, false);
   gemm_f64(c, 2, N, c->G1, c->Zb, c->Dg, 1.0, nullptr, 0.0, 0.0, true);
   rowdot_f64(c, c->Dg, c->Sb, c->dsd);
-  LAUNCH(k_group_q, (2 * c->nat + 255) / 256, 256, 0, c->st, c->nat, c->G, c->dsd, c->p.d0_s,
-         c->p.d0_p, c->p.d0_d, c->q);
+  general_group_q(c);
   // S-weighted susceptibility diagonal: (Z beta D_perp (I - D_perp) Z S)_ii
   // with D_perp (I - D_perp) = (I - T^2) / 4
   gemm_f64(c, 2, N, T, T, c->Sm, 1.0, nullptr, 0.0, 0.0, true);
@@ -354,13 +385,16 @@ __global__ void k_response_stats_gen(int nat, int G, const double* __restrict__ 
   }
 }
 
+void general_response_stats(sxl_ctx* c, double* qv, double* dmu_dev) {
+  LAUNCH(k_response_stats_gen, 1, 1024, 0, c->st, c->nat, c->G, c->diagT + 2 * c->N, c->chi,
+         c->av, c->chiS, qv, dmu_dev);
+}
+
 int general_response(sxl_ctx* c, const double* v, double* qv, double* dmu_dev) {
-  const int N = c->N, G = c->G;
+  const int N = c->N;
   const size_t nn = (size_t)N * N;
-  const int wpb = 8;
   double* dv = c->du;  // 2 N orbital potentials of the direction
-  LAUNCH(k_potentials, (c->nat + wpb - 1) / wpb, 32 * wpb, 0, c->st, c->nat, G, c->gamma_m, v,
-         G == 3 ? c->p.J_l[0] : 0.5 * c->p.W, c->p.J_l[1], c->p.J_l[2], dv);
+  general_potentials(c, v, dv);
   LAUNCH(k_hbuild, (unsigned)((2 * nn + 255) / 256), 256, 0, c->st, N, (const double*)nullptr,
          c->Sb, dv, c->Mg);
   gemm_f64(c, 2, N, c->Zb, c->Mg, c->G1, 1.0, nullptr, 0.0, 0.0, false);
@@ -370,8 +404,7 @@ int general_response(sxl_ctx* c, const double* v, double* qv, double* dmu_dev) {
   gemm_f64(c, 2, N, c->Zb, c->dTa, c->G1, 1.0, nullptr, 0.0, 0.0, false);
   gemm_f64(c, 2, N, c->G1, c->Zb, c->X1, 1.0, nullptr, 0.0, 0.0, true);
   rowdot_f64(c, c->X1, c->Sb, c->av);
-  LAUNCH(k_response_stats_gen, 1, 1024, 0, c->st, c->nat, G, c->diagT + 2 * N, c->chi, c->av,
-         c->chiS, qv, dmu_dev);
+  general_response_stats(c, qv, dmu_dev);
   return SXL_OK;
 }
 
@@ -411,13 +444,21 @@ int general_forces(sxl_ctx* c, const double* R, const double* n, double* F, doub
   gemm_f64(c, 2, N, c->T[nr], c->Hp, c->P, -0.5, c->Hp, 0.5, 0.0, false);
   gemm_f64(c, 2, N, c->Zb, c->P, c->G1, 1.0, nullptr, 0.0, 0.0, false);
   gemm_f64(c, 2, N, c->G1, c->Zb, c->X0, 1.0, nullptr, 0.0, 0.0, true);
-  LAUNCH(k_force_mats, (unsigned)((nn + 255) / 256), 256, 0, c->st, N, c->Dg, c->vorb, c->X0,
-         c->Mg, c->Mg + nn);
+  general_forces_tail(c, R, n, c->X0, F, erep_atom);
+  return SXL_OK;
+}
+
+// the force kernel from D (Dg), the orbital potentials and W^sigma (2 x N x N)
+void general_forces_tail(sxl_ctx* c, const double* R, const double* n, const double* W,
+                         double* F, double* erep) {
+  const int N = c->N;
+  const size_t nn = (size_t)N * N;
+  LAUNCH(k_force_mats, (unsigned)((nn + 255) / 256), 256, 0, c->st, N, c->Dg, c->vorb, W, c->Mg,
+         c->Mg + nn);
   double* qtot = c->av;
   double* ntot = c->av + c->nat;
   LAUNCH(k_atom_totals, (c->nat + 255) / 256, 256, 0, c->st, c->nat, c->G, c->q, n, qtot, ntot);
-  launch_forces_general(c, R, c->Mg, c->Mg + nn, qtot, ntot, F, erep_atom);
-  return SXL_OK;
+  launch_forces_general(c, R, c->Mg, c->Mg + nn, qtot, ntot, F, erep);
 }
 
 // out[0] = E_coul = 1/2 sum_I (2 q_I - n_I) (gamma n)_I, out[1] = E_spin =

@@ -593,7 +593,7 @@ static int tc_bk(bool split) {
 static int gemm_tc_range(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C, float alpha,
                          const MatH* E, float beta, float gamma, bool sym, bool split, int kb0,
                          int nkb) {
-  const bool bf16 = c->p.precision == SXL_MIXED_BF16;
+  const bool bf16 = pairs_bf16(c);
   const int n = c->Np;
   // per-context choices (sxl_autotune) before the library defaults
   const int bk_ctx = split ? c->tc_bk_split : c->tc_bk_plain;
@@ -684,7 +684,7 @@ int gemm_tc_k(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C, float alp
 // parts), one pass over the concatenated K dimension.
 int gemm_tc_dual(sxl_ctx* c, const MatH& A1, const MatH& B1, const MatH& A2, const MatH& B2,
                  const MatH& C, float alpha, const MatH* E, float beta, float gamma, bool sym) {
-  const bool bf16 = c->p.precision == SXL_MIXED_BF16;
+  const bool bf16 = pairs_bf16(c);
   const int cps = tc_cps();
   const int n = c->Np, bk = 64;
   const int mt = cps == 2 ? 1 : (c->tc_mt_dual ? c->tc_mt_dual : 2);
@@ -906,7 +906,7 @@ __global__ void k_d_from_t_h(size_t nn, const uint16_t* hi, const uint16_t* lo, 
 // dispatch helpers (BF16 template chosen at run time)
 #define DISPATCH(c, KERN, grid, block, smem, ...)                                   \
   do {                                                                              \
-    if ((c)->p.precision == SXL_MIXED_BF16)                                         \
+    if (pairs_bf16(c))                                                              \
       LAUNCH(KERN<true>, grid, block, smem, (c)->st, __VA_ARGS__);                  \
     else                                                                            \
       LAUNCH(KERN<false>, grid, block, smem, (c)->st, __VA_ARGS__);                 \
@@ -977,7 +977,7 @@ __global__ void k_symcombo2_h(int n, uint16_t* ohi, uint16_t* olo, float a, cons
   }
 }
 
-static void symcombo_h(sxl_ctx* c, const MatH& out, double a, const MatH* X, double b,
+void symcombo_h(sxl_ctx* c, const MatH& out, double a, const MatH* X, double b,
                        const MatH* Y, double cc, const double* w, const MatH* Z) {
   int n = c->Np;  // the chain dimension is a multiple of 64
   dim3 grid(n / 64, n / 32, 2), block(32, 8);
@@ -1004,7 +1004,7 @@ __global__ void k_axpy_diag2_h(size_t groups, int n, uint16_t* ohi, uint16_t* ol
   st8<BF16>(ohi, olo, i, v);
 }
 
-static void axpy_diag_h(sxl_ctx* c, const MatH& out, double a, const MatH& X, double g) {
+void axpy_diag_h(sxl_ctx* c, const MatH& out, double a, const MatH& X, double g) {
   size_t groups = (size_t)c->Np * c->Np / 4;  // 2 spins x Np^2 / 8
   DISPATCH(c, k_axpy_diag2_h, (unsigned)((groups + 255) / 256), 256, 0, groups, c->Np, out.hi,
            out.lo, (float)a, X.hi, X.lo, (float)g);
@@ -1067,7 +1067,21 @@ __global__ void k_apm_h(size_t pairs, uint16_t* yhi, uint16_t* ylo, const uint16
   st_pair<BF16>(mhi, mlo, i, y0 - 0.5f * t0, y1 - 0.5f * t1);
 }
 
-static int halloc(sxl_ctx* c, MatH* m) {
+// diag(T) (and, if rowsq is not null, the row norms) of the n real rows of
+// both spins: outputs indexed spin * n + row
+void rowstats_h(sxl_ctx* c, const MatH& T, double* diag, double* rowsq) {
+  const int wpb = 8, rows = 2 * c->N;
+  DISPATCH(c, k_rowstats_h, (rows + wpb - 1) / wpb, 32 * wpb, 0, c->Np, c->N, T.hi, T.lo, diag,
+           rowsq);
+}
+// out[s n + r] = scale sum_j A[s][r][j] B[s][r][j] for the n real rows
+void rowdot_h(sxl_ctx* c, const MatH& A, const MatH& B, double scale, double* out) {
+  const int wpb = 8;
+  DISPATCH(c, k_rowdot2_h, (2 * c->N + wpb - 1) / wpb, 32 * wpb, 0, c->Np, c->N, A.hi, A.lo, B.hi,
+           B.lo, scale, out);
+}
+
+int halloc(sxl_ctx* c, MatH* m) {
   size_t n = 2 * (size_t)c->Np * c->Np;
   m->hi = m->lo = nullptr;
   if (cudaMalloc((void**)&m->hi, n * 2) != cudaSuccess ||
@@ -1077,7 +1091,7 @@ static int halloc(sxl_ctx* c, MatH* m) {
   CUDA_TRY(c, cudaMemsetAsync(m->lo, 0, n * 2, c->st));
   return SXL_OK;
 }
-static void hfree(MatH& m) {
+void hfree(MatH& m) {
   if (m.hi) cudaFree(m.hi);
   if (m.lo) cudaFree(m.lo);
   m.hi = m.lo = nullptr;
@@ -1106,6 +1120,11 @@ int sxl_mixed_supported(sxl_ctx* c) {
   MatH* ms[] = {&c->hU, &c->hS, &c->hQ, &c->hX0, &c->hX1, &c->hP, &c->hSm, &c->hdTa, &c->hdTb, &c->hG1,
                 &c->hTeff};
   for (MatH* m : ms) SXL_TRY(halloc(c, m));
+  c->hZg.hi = c->hZg.lo = c->hSh.hi = c->hSh.lo = c->hHp.hi = c->hHp.lo = nullptr;
+  if (c->general) {
+    MatH* gs[] = {&c->hZg, &c->hSh, &c->hHp};
+    for (MatH* m : gs) SXL_TRY(halloc(c, m));
+  }
   CUDA_TRY(c, cudaMalloc((void**)&c->dup, 2 * (size_t)c->Np * sizeof(double)));
   c->teff_valid = false;
   return SXL_OK;
@@ -1113,7 +1132,7 @@ int sxl_mixed_supported(sxl_ctx* c) {
 
 void sxl_mixed_free(sxl_ctx* c) {
   MatH* ms[] = {&c->hU, &c->hS, &c->hQ, &c->hX0, &c->hX1, &c->hP, &c->hSm, &c->hdTa, &c->hdTb, &c->hG1,
-                &c->hTeff};
+                &c->hTeff, &c->hZg, &c->hSh, &c->hHp};
   for (MatH* m : ms) hfree(*m);
   if (c->fscratch) cudaFree(c->fscratch);
   c->fscratch = nullptr;
@@ -1228,8 +1247,11 @@ int foe_mixed(sxl_ctx* c, double mu, double* stats_dev) {
   // padding orbitals (Np > N) sit at the upper spectral bound: |u| <= umax,
   // and with mu inside the spectrum they stay empty (f ~ exp(-beta (lam_max - mu)))
   size_t total = (size_t)Np * Np;
-  DISPATCH(c, k_build_u_h, (unsigned)((total + 255) / 256), 256, 0, c->nat, Np, c->H0, c->shift, mu,
-           c->scale, c->lam_max, c->hU.hi, c->hU.lo);
+  if (c->general)
+    build_u_general_h(c, mu, c->scale, c->lam_max);
+  else
+    DISPATCH(c, k_build_u_h, (unsigned)((total + 255) / 256), 256, 0, c->nat, Np, c->H0, c->shift,
+             mu, c->scale, c->lam_max, c->hU.hi, c->hU.lo);
   SXL_TRY(gemm_tc_k(c, c->hU, c->hU, c->hS, 1.f, nullptr, 0.f, 0.f, true, split, kc, tmp));
   SXL_TRY(gemm_tc_k(c, c->hS, c->hS, c->hQ, (float)(2.0 / 15.0), &c->hS, (float)(-1.0 / 3.0), 1.f,
                     true, split, kc, tmp));
@@ -1321,7 +1343,25 @@ int mu_shift_mixed(sxl_ctx* c, double dmu, double* stats_dev) {
   return SXL_OK;
 }
 
+// The first-order response of the chain.  du_real: the orthogonal model's
+// diagonal perturbation (scaled, per orbital).  For the general model
+// (v_gen != null, a direction of the extended vector) the start is the
+// dense perturbation Z dH Z, the last step is formed in full and the
+// response's occupations come from general_response_end_mixed into
+// qv / dmu_dev.
+static int dmpt_mixed_impl(sxl_ctx* c, const double* du_real, const double* v_gen, double* qv,
+                           double* dmu_dev);
+
 int dmpt_mixed(sxl_ctx* c, const double* du_real) {
+  return dmpt_mixed_impl(c, du_real, nullptr, nullptr, nullptr);
+}
+
+int dmpt_mixed_general(sxl_ctx* c, const double* v, double* qv, double* dmu_dev) {
+  return dmpt_mixed_impl(c, nullptr, v, qv, dmu_dev);
+}
+
+static int dmpt_mixed_impl(sxl_ctx* c, const double* du_real, const double* v_gen, double* qv,
+                           double* dmu_dev) {
   const int N = c->N, Np = c->Np, nr = c->nr;
   // The response products run on the hi parts alone (fp16/bf16 operands,
   // fp32 accumulation; one product per k step): the relative error of q_v is
@@ -1333,6 +1373,11 @@ int dmpt_mixed(sxl_ctx* c, const double* du_real) {
     return (e && atoi(e) == 1) ? 1 : 0;
   }();
   const bool split = use_split == 1;
+  const MatH* dA = &c->hdTa;
+  const MatH* dB = &c->hdTb;
+  if (v_gen) {
+    SXL_TRY(general_response_start_mixed(c, v_gen, *dA));
+  } else {
   // the perturbation on the chain dimension (zero on the padding)
   double* du = c->dup;
   LAUNCH(k_pad_vec, (2 * Np + 255) / 256, 256, 0, c->st, N, Np, du_real, du);
@@ -1348,9 +1393,8 @@ int dmpt_mixed(sxl_ctx* c, const double* du_real) {
                          (float)(-1.0 / 3.0), 0.f, true));
   }
   SXL_TRY(gemm_tc(c, c->hU, c->hP, c->hG1, 1.f, nullptr, 0.f, 0.f, false, split));
-  const MatH* dA = &c->hdTa;
-  const MatH* dB = &c->hdTb;
   symcombo_h(c, *dA, 0.0, nullptr, 0.5, &c->hG1, 0.5, du, &c->hQ);
+  }
   // Step k of the chain in sandwich form.  In the common eigenbasis
   //   dT_{k+1}[a,b] = 2 dT_k[a,b] y_a y_b (1 - t_a t_b),
   // and 2 y_a y_b (1 - t_a t_b) = y_a (1 - t_a) y_b (1 + t_b) + y_a (1 + t_a) y_b (1 - t_b),
@@ -1393,6 +1437,12 @@ int dmpt_mixed(sxl_ctx* c, const double* du_real) {
     std::swap(dA, dB);
   }
   SXL_TRY(gemm_tc(c, c->hY[nr - 1], *dA, c->hG1, 1.f, nullptr, 0.f, 0.f, false, split));
+  if (v_gen) {
+    // the general model needs the whole dT_nr (its occupations are S-weighted)
+    SXL_TRY(gemm_tc_dual(c, c->hAm[nr - 1], c->hG1, c->hG1, c->hAm[nr - 1], *dB, 1.f, nullptr, 0.f,
+                         0.f, true));
+    return general_response_end_mixed(c, *dB, qv, dmu_dev);
+  }
   DISPATCH(c, k_rowdot2_h, (2 * N + wpb - 1) / wpb, 32 * wpb, 0, Np, N, c->hAm[nr - 1].hi,
            c->hAm[nr - 1].lo, c->hG1.hi, c->hG1.lo, 2.0, c->diagT + 2 * N);
   return SXL_OK;

@@ -260,9 +260,18 @@ def fe128_general() -> Workload:
     return w
 
 
+def fe1024_general() -> Workload:
+    """The 1024-atom cell of the general model (overlap, shells resolved)."""
+    w = fe1024()
+    w.params = general_model(w.params)
+    w.n0 = shell_resolved_n(w.n0)
+    w.name = "fe1024_bcc8x8x8_general"
+    return w
+
+
 WORKLOADS = {"fe16": fe16, "fe128": fe128, "fe1024": fe1024, "fe2000": fe2000,
              "fe16_general": fe16_general, "fe54_general": fe54_general,
-             "fe128_general": fe128_general}
+             "fe128_general": fe128_general, "fe1024_general": fe1024_general}
 
 
 def random_direction(n_atoms: int, seed: int) -> np.ndarray:

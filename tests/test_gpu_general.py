@@ -11,6 +11,10 @@ parameters (Sec. II.C, Sec. III.A), against the general oracle
 * Ten sXL-BOMD steps of the 16-atom cell from its unconverged start
   (K0 = -I): positions, velocities and n step by step.
 Tolerances: the fp64 form's 1e-10 e and 1e-8 eV/A.
+
+The mixed forms (fp16, bf16) of the same model: single points at 16 and
+54 atoms and 60-step runs checked at three states, with the mixed bars
+(1e-4 e, 1e-3 eV/A).
 """
 import numpy as np
 import pytest
@@ -92,3 +96,116 @@ def test_general_xlbomd_steps(sxl):
         assert abs(mu - st_o["mu"]) < 1e-9
         assert abs(st[0] - st_o["Etot"]) < 1e-8 * nat
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("wname", ["fe16_general", "fe54_general"])
+def test_general_mixed_against_oracle(sxl, wname, prec):
+    """The general model in the mixed forms (Z = S^{-1/2} by Newton-Schulz in
+    split products, H_perp = Z H Z and every chain product on the tensor
+    cores): q and m per shell to 1e-4 e, forces to 1e-3 eV/A, the response
+    within the response products' bound (n_r + 2 steps of three roundings to
+    the 16-bit hi parts: the dense start adds two products), U within the
+    mixed form's bars."""
+    w = getattr(wl, wname)()
+    p, nat = w.params, w.n_atoms
+    d = general.density(w.R, w.cell, w.n0, p)
+    ctx = sxl.Context(p, nat, w.cell, prec)
+    q, mu = ctx.density(w.R, w.n0)
+    q = q.cpu().numpy()
+    G = 3 * nat
+    err_q = np.abs(q - d.q).max()
+    err_m = np.abs((q[:G] - q[G:]) - d.spin).max()
+    print(f"{wname} {prec}: |dq| {err_q:.2e} |dm| {err_m:.2e} |dmu| {abs(mu - d.mu):.2e} "
+          f"sum(q) - N_e {q.sum() - d.q.sum():.2e} mu {d.mu:.3f}")
+    assert err_q < 1e-4 and err_m < 1e-4
+    v = wl.random_direction(3 * nat, 5)
+    qv, _ = ctx.response(v)
+    qv_o, _ = d.response(v)
+    rel = np.abs(qv.cpu().numpy() - qv_o).max() / np.abs(qv_o).max()
+    u = 2.0 ** -12 if prec == "fp16" else 2.0 ** -9
+    bound = (ctx.info()["foe_steps"] + 2) * 3 * u
+    print(f"{wname} {prec}: response rel err {rel:.2e} (bound {bound:.2e})")
+    assert rel < bound
+    F, en = ctx.forces(w.R, w.n0, energies=True)
+    F_o = general.forces(d, w.R, w.cell)
+    e_o = general.shadow_energy(d, model.build_h0(w.R, w.cell, p),
+                                model.repulsive_energy(w.R, w.cell, p))
+    err_f = np.abs(F.cpu().numpy() - F_o).max()
+    d_u = abs(en["U"] - e_o["U"]) / nat
+    print(f"{wname} {prec}: |dF| {err_f:.2e} dU/atom {d_u:.2e}")
+    assert err_f < 1e-3
+    assert d_u < (1e-3 if prec == "fp16" else 5e-3)
+    ctx.close()
+
+
+def _md_states(sxl, prec, steps=60, every=30):
+    """MD from the SCF point at n = 0 (see the test); returns the checks at
+    each state and the run's total energies and largest residual."""
+    w = wl.fe16_general()
+    p, nat = w.params, w.n_atoms
+    G = 3 * nat
+    ctx = sxl.Context(p, nat, w.cell, prec)
+    n_star, iters, rms, _ = ctx.scf_ex(w.R, np.zeros(ctx.n2), tol=1e-5, max_iter=40,
+                                       mixer="kernel", switch_rms=1.0)
+    _, mu = ctx.density(w.R, n_star)
+    ctx.set_state(w.R, w.V, torch.stack([n_star] * (p.kmax + 1)).contiguous(), mu)
+    probe = sxl.Context(p, nat, w.cell, prec)
+    E, rmsmax, checks = [], 0.0, []
+    for s in range(0, steps + 1, every):
+        if s > 0:
+            for st in ctx.step(every, stats=True):
+                E.append(st[0])
+                rmsmax = max(rmsmax, st[2])
+        R, V, nh, mu_s = ctx.get_state()
+        R, n = R.cpu().numpy(), nh[0].cpu().numpy()
+        q, _ = probe.density(R, n, mu_s)
+        F, en = probe.forces(R, n, energies=True)
+        q, F = q.cpu().numpy(), F.cpu().numpy()
+        d = general.density(R, w.cell, n, p, mu_guess=mu_s)
+        F_o = general.forces(d, R, w.cell)
+        U_o = general.shadow_energy(d, model.build_h0(R, w.cell, p),
+                                    model.repulsive_energy(R, w.cell, p))["U"]
+        checks.append((s, np.abs(q - d.q).max(), np.abs((q[:G] - q[G:]) - d.spin).max(),
+                       np.abs(F - F_o).max(), abs(en["U"] - U_o) / nat))
+    probe.close()
+    ctx.close()
+    return checks, np.array(E) / nat, rmsmax, iters
+
+
+def test_general_md_states_every_form(sxl):
+    """60 MD steps of the 16-atom general cell in each form (fp64, fp16,
+    bf16) from the form's SCF point: from n = 0 (the non-magnetic solution),
+    the kernel mixer from the first iteration with the exact K0 = J^-1
+    there, to RMS(q - n) < 1e-5; the run keeps that K0.  (The l-dependent
+    Stoner terms leave J with eigenvalues of both signs about this state;
+    Newton's method reaches it in three iterations, while a rank-m mixer on
+    K0 = -I from a random start can stall.)
+
+    A mixed trajectory is not compared with the oracle's step by step (the
+    rank-m least-squares fit of the Krylov kernel is ill-conditioned, so
+    rounding moves n visibly within a few steps while both runs stay on
+    their shadow surfaces).  Instead, at steps 0, 30 and 60 the library's q,
+    m, forces and U at the trajectory's (R, n) are checked against the
+    general oracle at the same (R, n), with the form's bars; the residual
+    RMS(q - n) stays below 1e-3; and the spread (max - min) of the total
+    energy per atom over the run stays within the fp64 run's spread plus
+    twice the form's U bar (the energy of each step carries the form's
+    error of U)."""
+    bars = {"fp64": (1e-10, 1e-8, 1e-8), "fp16": (1e-4, 1e-3, 1e-3), "bf16": (1e-4, 1e-3, 5e-3)}
+    spread = {}
+    for prec in ("fp64", "fp16", "bf16"):
+        checks, E, rmsmax, iters = _md_states(sxl, prec)
+        tq, tf, tu = bars[prec]
+        for s, eq, em, ef, eu in checks:
+            print(f"general {prec} step {s}: |dq| {eq:.2e} |dm| {em:.2e} |dF| {ef:.2e} "
+                  f"dU/atom {eu:.2e}")
+            assert eq < tq and em < tq
+            assert ef < tf
+            assert eu < tu
+        spread[prec] = E.max() - E.min()
+        print(f"general {prec}: SCF {iters} it, max RMS(q - n) {rmsmax:.2e}, "
+              f"E spread {spread[prec]:.2e} eV/atom")
+        assert rmsmax < 1e-3
+        if prec != "fp64":
+            assert spread[prec] < spread["fp64"] + 2 * tu
