@@ -146,9 +146,9 @@ def traffic_record():
     from single-launch captures of `bench.py --gemm-only` (profiles/
     tc_gemm_traffic.json), scaled to the workload's matrix size; None when
     the record was taken on other kernel code (the record holds the hash of
-    the source it was captured on)."""
+    the kernel's source file, tc_gemm.cuh, it was captured on)."""
     path = os.path.join(ROOT, "profiles", "tc_gemm_traffic.json")
-    src = os.path.join(ROOT, "paper_2303_03529_gb300", "csrc", "mixed.cu")
+    src = os.path.join(ROOT, "paper_2303_03529_gb300", "csrc", "tc_gemm.cuh")
     if not os.path.exists(path):
         return None
     with open(path) as f:
