@@ -279,20 +279,29 @@ int sxl_mixed_gemm(sxl_ctx* ctx, const double* A_dev, const double* B_dev, const
  * (no counterpart in the paper; the tile shapes of the batched form).  Times
  * every candidate tile of the three product forms on the context's own
  * chain buffers with CUDA events (3 launches each, after a warm-up): plain
- * products over K blocks of 64 or 32 and 256- or 128-row tiles, split
- * products over K blocks of 32 or 64, dual products over 256- or 128-row
- * tiles; keeps the fastest for this context.  out7_host (may be NULL)
- * receives [plain K block, plain rows/128, plain ms, split K block, split ms,
- * dual rows/128, dual ms].  Discards any density the context held.
- * SXL_E_STATE for an fp64 context. */
-int sxl_autotune(sxl_ctx* ctx, double* out7_host);
+ * products over K blocks of 64 or 32 and 256- or 128-row tiles and on the
+ * persistent kernel, split products over K blocks of 32 or 64, dual
+ * products over 256- or 128-row tiles and on the persistent kernel; keeps
+ * the fastest for this context.  out9_host (may be NULL) receives [plain K
+ * block, plain rows/128, plain ms, split K block, split ms, dual rows/128,
+ * dual ms, plain on the persistent kernel (0/1), dual on the persistent
+ * kernel (0/1)].  Discards any density the context held.  SXL_E_STATE for
+ * an fp64 context. */
+int sxl_autotune(sxl_ctx* ctx, double* out9_host);
 /* Sets the tile choices directly (0 = library default): plain K block 32 or
  * 64, plain rows per CTA 1 or 2 (x 128), split K block 32 or 64, dual rows
  * per CTA 1 or 2.  SXL_E_ARG for other values. */
 int sxl_set_tiles(sxl_ctx* ctx, int bk_plain, int mt_plain, int bk_split, int mt_dual);
+/* Kernel of the plain and dual products (the response chain): 1 = the
+ * persistent kernel (one CTA per SM walking 256 x 128 output tiles, two TMEM
+ * accumulator stages, so that a tile's epilogue overlaps the next tile's
+ * MMAs), 2 = the single-tile kernel (one CTA per output tile, the tiles of
+ * sxl_set_tiles), 0 = library default.  The environment variable SXL_TC_PS
+ * (1 or 0) overrides the choice.  SXL_E_ARG for other values. */
+int sxl_set_product_kernel(sxl_ctx* ctx, int kernel);
 /* Autotunes every replica of a batch; replicas with the same chain
- * dimension share one tuning run.  report_host (may be NULL, 8 doubles per
- * distinct dimension) receives [chain dimension, the 7 values of
+ * dimension share one tuning run.  report_host (may be NULL, 10 doubles per
+ * distinct dimension) receives [chain dimension, the 9 values of
  * sxl_autotune].  Returns the number of distinct dimensions tuned (>= 1), or
  * a negative SXL_E_* code. */
 int sxl_batch_autotune(sxl_batch* batch, double* report_host);

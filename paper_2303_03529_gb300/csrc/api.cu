@@ -1009,14 +1009,14 @@ int sxl_mixed_gemm(sxl_ctx* c, const double* A, const double* B, const double* E
   return SXL_OK;
 }
 
-int sxl_autotune(sxl_ctx* c, double* out7) {
+int sxl_autotune(sxl_ctx* c, double* out9) {
   if (!c) return SXL_E_ARG;
   if (c->p.precision == SXL_FP64) return sxl_fail(c, SXL_E_STATE, "context is fp64");
   // the timing runs in the chain's buffers: the density is gone
   c->have_density = false;
   c->apm_ready = false;
   c->teff_valid = false;
-  SXL_TRY(mixed_autotune(c, out7));
+  SXL_TRY(mixed_autotune(c, out9));
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   int flag = 0;
   SXL_TRY(tc_error_flag(c, &flag));
@@ -1034,6 +1034,13 @@ int sxl_set_tiles(sxl_ctx* c, int bk_plain, int mt_plain, int bk_split, int mt_d
   c->tc_mt_plain = mt_plain;
   c->tc_bk_split = bk_split;
   c->tc_mt_dual = mt_dual;
+  return SXL_OK;
+}
+
+int sxl_set_product_kernel(sxl_ctx* c, int kernel) {
+  if (!c) return SXL_E_ARG;
+  if (kernel < 0 || kernel > 2) return sxl_fail(c, SXL_E_ARG, "product kernel out of range");
+  c->tc_ps_plain = c->tc_ps_dual = kernel;
   return SXL_OK;
 }
 

@@ -83,7 +83,7 @@ int sxl_batch_step(sxl_batch* b, int nsteps, int nthreads, int* status) {
 // one tuning run (the first of them is timed, the others take its choice).
 int sxl_batch_autotune(sxl_batch* b, double* report_host) {
   if (!b) return SXL_E_ARG;
-  std::vector<std::pair<int, std::array<int, 4>>> done;  // (Np, choice)
+  std::vector<std::pair<int, std::array<int, 6>>> done;  // (Np, choice)
   int k = 0;
   for (size_t i = 0; i < b->ctx.size(); ++i) {
     sxl_ctx* c = b->ctx[i];
@@ -91,17 +91,20 @@ int sxl_batch_autotune(sxl_batch* b, double* report_host) {
     for (auto& d : done)
       if (d.first == c->Np) {
         SXL_TRY(sxl_set_tiles(c, d.second[0], d.second[1], d.second[2], d.second[3]));
+        c->tc_ps_plain = d.second[4];
+        c->tc_ps_dual = d.second[5];
         found = true;
         break;
       }
     if (found) continue;
-    double out[7];
+    double out[9];
     SXL_TRY(sxl_autotune(c, out));
-    done.push_back({c->Np, {(int)out[0], (int)out[1], (int)out[3], (int)out[5]}});
+    done.push_back({c->Np, {(int)out[0], (int)out[1], (int)out[3], (int)out[5],
+                            c->tc_ps_plain, c->tc_ps_dual}});
     if (report_host) {
-      double* r = report_host + 8 * k;
+      double* r = report_host + 10 * k;
       r[0] = c->Np;
-      for (int j = 0; j < 7; ++j) r[1 + j] = out[j];
+      for (int j = 0; j < 9; ++j) r[1 + j] = out[j];
     }
     ++k;
   }

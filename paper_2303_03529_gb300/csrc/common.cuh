@@ -73,6 +73,8 @@ struct sxl_ctx {
   // tile choices of the tensor-core GEMM for this context (0: library
   // default); set by sxl_autotune / sxl_set_tiles
   int tc_bk_plain, tc_mt_plain, tc_bk_split, tc_mt_dual;
+  // plain and dual products: 1 persistent kernel, 2 single-tile, 0 default
+  int tc_ps_plain = 0, tc_ps_dual = 0;
   // true while the general model's overlap-side products (those with Z or
   // S^{1/2}) run: they take fp16 pairs in the bf16 form too (general_mixed.cu)
   bool pairs_fp16 = false;

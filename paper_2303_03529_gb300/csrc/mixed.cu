@@ -29,6 +29,7 @@
 #include <mutex>
 
 #include "tc_gemm.cuh"
+#include "tc_gemm_ps.cuh"
 
 // ---------------------------------------------------------------------------
 // host side: tensor maps and launch
@@ -105,6 +106,63 @@ static int launch_tc(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a) {
   return SXL_OK;
 }
 
+// The persistent plain/dual product (tc_gemm_ps.cuh): one CTA per SM, or
+// one per owned tile when there are fewer.
+template <bool BF16, bool DUAL>
+static int launch_tc_ps(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a) {
+  static std::atomic<bool> attr{false};
+  if (!attr.load()) {
+    CUDA_TRY(c, cudaFuncSetAttribute(k_tc_gemm_ps<BF16, DUAL>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)PsCfg::SMEM));
+    attr.store(true);
+  }
+  int dev = 0, nsm = 0;
+  CUDA_TRY(c, cudaGetDevice(&dev));
+  CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  PsArgs pa;
+  pa.g = a;
+  pa.tiles = 0;  // tiles of one spin block: all, or those a symmetric product owns
+  for (int tm = 0; tm < a.ntm; ++tm)
+    pa.tiles += a.sym ? std::max(0, a.ntn - 2 * tm) : a.ntn;
+  const double tiles = pa.tiles;
+  const int grid = std::max(1, std::min(nsm, 2 * pa.tiles));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->time_tc) {
+    e0 = ev_get(c);
+    e1 = ev_get(c);
+    CUDA_TRY(c, cudaEventRecord(e0, c->st));
+  }
+  k_tc_gemm_ps<BF16, DUAL><<<grid, 192, PsCfg::SMEM, c->st>>>(maps[0], maps[1], maps[2],
+                                                              maps[3], pa);
+  ++g_sxl_launches;
+  if (c->time_tc) {
+    CUDA_TRY(c, cudaEventRecord(e1, c->st));
+    const double n = a.n;
+    const double kdim = (double)a.nk * PS_BK;
+    const double mma = 2.0 * tiles * 2.0 * PS_BM * PS_BN * kdim;
+    const double owned = a.sym ? n * (n + 1) / 2 : n * n;
+    const double f32 = 2.0 * 2.0 * owned * kdim;
+    c->ev_pending.push_back({e0, e1, mma, f32, f32, DUAL ? 1 : 0});
+  }
+  return SXL_OK;
+}
+
+// Plain (dual = false) or dual products on the persistent kernel:
+// SXL_TC_PS=1 or 0 forces the choice, else the context's
+// (sxl_set_product_kernel / sxl_autotune), else the library default, the
+// single-tile kernel (faster at the benchmark's n = 9216; the persistent one
+// wins on plain products up to n = 4608, where it has more tiles per SM).
+static bool use_ps(const sxl_ctx* c, bool dual) {
+  static const int env = [] {
+    const char* e = getenv("SXL_TC_PS");
+    return e ? atoi(e) : -1;
+  }();
+  if (env == 0 || env == 1) return env == 1;
+  const int k = dual ? c->tc_ps_dual : c->tc_ps_plain;
+  return k == 1;
+}
+
 // C = alpha A B^T + beta E + gamma I for both spins; split selects the
 // three-product form.  Matrices are n x n with n % 64 == 0.
 // K-block per product form (measured at n = 9216): split products run best
@@ -128,15 +186,21 @@ static int tc_bk(bool split) {
   return (bk_env == 32 || bk_env == 64) ? bk_env : (split ? 32 : 64);
 }
 
+// The K block of a product form on this context: its own choice
+// (sxl_autotune / sxl_set_tiles) before the library default.  kb0 and nkb of
+// gemm_tc_range count blocks of this width.
+static int tc_bk_ctx(const sxl_ctx* c, bool split) {
+  const int bk = split ? c->tc_bk_split : c->tc_bk_plain;
+  return bk ? bk : tc_bk(split);
+}
+
 // The product over the k blocks [kb0, kb0 + nkb) of K (nkb = 0: all of K).
 static int gemm_tc_range(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C, float alpha,
                          const MatH* E, float beta, float gamma, bool sym, bool split, int kb0,
                          int nkb) {
   const bool bf16 = pairs_bf16(c);
   const int n = c->Np;
-  // per-context choices (sxl_autotune) before the library defaults
-  const int bk_ctx = split ? c->tc_bk_split : c->tc_bk_plain;
-  const int bk = bk_ctx ? bk_ctx : tc_bk(split);
+  const int bk = tc_bk_ctx(c, split);
   // plain products cover 256 rows per CTA (two M = 128 MMAs per B tile);
   // SXL_TC_MT=1 restores 128-row tiles
   static const int mt_env = [] {
@@ -146,16 +210,8 @@ static int gemm_tc_range(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C
   const int cps = split ? 1 : tc_cps();
   int mt = split ? 1 : ((mt_env == 1 || cps == 2) ? 1 : 2);
   if (!split && c->tc_mt_plain && cps == 1) mt = c->tc_mt_plain;
-  CUtensorMap maps[4];
-  SXL_TRY(make_map(c, &maps[0], A.hi, n, TC_BM * mt, bf16, bk));
-  SXL_TRY(make_map(c, &maps[1], A.lo, n, TC_BM * mt, bf16, bk));
-  SXL_TRY(make_map(c, &maps[2], B.hi, n, TC_BN, bf16, bk));
-  SXL_TRY(make_map(c, &maps[3], B.lo, n, TC_BN, bf16, bk));
   TcArgs a;
   a.n = n;
-  a.ntm = (n + TC_BM * mt - 1) / (TC_BM * mt);
-  a.ntn = (n + TC_BN - 1) / TC_BN;
-  a.nk = nkb > 0 ? nkb : n / bk;
   a.kb0 = kb0;
   a.nk_half = 0;
   a.alpha = alpha;
@@ -167,6 +223,32 @@ static int gemm_tc_range(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C
   a.Clo = C.lo;
   a.sym = sym ? 1 : 0;
   a.err = c->tc_err;
+  if (!split && use_ps(c, false)) {
+    CUtensorMap pm[4];
+    SXL_TRY(make_map(c, &pm[0], A.hi, n, PS_BM, bf16, PS_BK));
+    pm[1] = pm[0];
+    SXL_TRY(make_map(c, &pm[2], B.hi, n, PS_BN, bf16, PS_BK));
+    pm[3] = pm[2];
+    a.ntm = (n + PS_BM - 1) / PS_BM;
+    a.ntn = (n + PS_BN - 1) / PS_BN;
+    a.nk = nkb > 0 ? nkb : n / PS_BK;
+    if (kb0 * bk % PS_BK != 0 || (nkb > 0 && nkb * bk % PS_BK != 0))
+      return sxl_fail(c, SXL_E_ARG, "persistent product: K range not in 64-wide blocks");
+    if (nkb > 0) {
+      a.kb0 = kb0 * bk / PS_BK;
+      a.nk = nkb * bk / PS_BK;
+    }
+    c->n_gemm++;
+    return bf16 ? launch_tc_ps<true, false>(c, pm, a) : launch_tc_ps<false, false>(c, pm, a);
+  }
+  CUtensorMap maps[4];
+  SXL_TRY(make_map(c, &maps[0], A.hi, n, TC_BM * mt, bf16, bk));
+  SXL_TRY(make_map(c, &maps[1], A.lo, n, TC_BM * mt, bf16, bk));
+  SXL_TRY(make_map(c, &maps[2], B.hi, n, TC_BN, bf16, bk));
+  SXL_TRY(make_map(c, &maps[3], B.lo, n, TC_BN, bf16, bk));
+  a.ntm = (n + TC_BM * mt - 1) / (TC_BM * mt);
+  a.ntn = (n + TC_BN - 1) / TC_BN;
+  a.nk = nkb > 0 ? nkb : n / bk;
   c->n_gemm++;
   if (split) {
     if (bk == 64) return bf16 ? launch_tc<true, true, 64>(c, maps, a) : launch_tc<false, true, 64>(c, maps, a);
@@ -200,7 +282,7 @@ int gemm_tc(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C, float alpha
 int gemm_tc_k(sxl_ctx* c, const MatH& A, const MatH& B, const MatH& C, float alpha,
               const MatH* E, float beta, float gamma, bool sym, bool split, int chunks,
               const MatH& tmp) {
-  const int nkb = c->Np / tc_bk(split);
+  const int nkb = c->Np / tc_bk_ctx(c, split);
   if (chunks > nkb) chunks = nkb;
   if (chunks <= 1) return gemm_tc(c, A, B, C, alpha, E, beta, gamma, sym, split);
   const int per = (nkb + chunks - 1) / chunks;
@@ -227,6 +309,30 @@ int gemm_tc_dual(sxl_ctx* c, const MatH& A1, const MatH& B1, const MatH& A2, con
   const int cps = tc_cps();
   const int n = c->Np, bk = 64;
   const int mt = cps == 2 ? 1 : (c->tc_mt_dual ? c->tc_mt_dual : 2);
+  if (use_ps(c, true)) {
+    CUtensorMap pm[4];
+    SXL_TRY(make_map(c, &pm[0], A1.hi, n, PS_BM, bf16, PS_BK));
+    SXL_TRY(make_map(c, &pm[1], A2.hi, n, PS_BM, bf16, PS_BK));
+    SXL_TRY(make_map(c, &pm[2], B1.hi, n, PS_BN, bf16, PS_BK));
+    SXL_TRY(make_map(c, &pm[3], B2.hi, n, PS_BN, bf16, PS_BK));
+    TcArgs a;
+    a.n = n;
+    a.ntm = (n + PS_BM - 1) / PS_BM;
+    a.ntn = (n + PS_BN - 1) / PS_BN;
+    a.nk_half = n / PS_BK;
+    a.nk = 2 * a.nk_half;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.gamma = gamma;
+    a.Ehi = E ? E->hi : nullptr;
+    a.Elo = E ? E->lo : nullptr;
+    a.Chi = C.hi;
+    a.Clo = C.lo;
+    a.sym = sym ? 1 : 0;
+    a.err = c->tc_err;
+    c->n_gemm++;
+    return bf16 ? launch_tc_ps<true, true>(c, pm, a) : launch_tc_ps<false, true>(c, pm, a);
+  }
   CUtensorMap maps[4];
   SXL_TRY(make_map(c, &maps[0], A1.hi, n, TC_BM * mt, bf16, bk));
   SXL_TRY(make_map(c, &maps[1], A2.hi, n, TC_BM * mt, bf16, bk));
@@ -301,13 +407,14 @@ int mixed_autotune(sxl_ctx* c, double* out) {
   LAUNCH(k_fill_pattern, (unsigned)((nn + 255) / 256), 256, 0, c->st, nn, c->hU.hi, c->hU.lo, bf16);
   LAUNCH(k_fill_pattern, (unsigned)((nn + 255) / 256), 256, 0, c->st, nn, c->hS.hi, c->hS.lo, bf16);
   const int reps = 3;
-  // plain: (K block, rows per CTA)
-  const int pc[4][2] = {{64, 2}, {64, 1}, {32, 2}, {32, 1}};
+  // plain: (K block, rows per CTA, persistent kernel)
+  const int pc[5][3] = {{64, 2, 2}, {64, 1, 2}, {32, 2, 2}, {32, 1, 2}, {64, 2, 1}};
   float best = 1e30f;
   int bi = 0;
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 5; ++i) {
     c->tc_bk_plain = pc[i][0];
     c->tc_mt_plain = pc[i][1];
+    c->tc_ps_plain = pc[i][2];
     float ms = 0.f;
     SXL_TRY(time_launches(c, [&] { return gemm_tc(c, c->hU, c->hS, c->hG1, 1.f, nullptr, 0.f, 0.f,
                                                   false, false); }, reps, &ms));
@@ -315,7 +422,8 @@ int mixed_autotune(sxl_ctx* c, double* out) {
   }
   c->tc_bk_plain = pc[bi][0];
   c->tc_mt_plain = pc[bi][1];
-  if (out) { out[0] = pc[bi][0]; out[1] = pc[bi][1]; out[2] = best; }
+  c->tc_ps_plain = pc[bi][2];
+  if (out) { out[0] = pc[bi][0]; out[1] = pc[bi][1]; out[2] = best; out[7] = pc[bi][2] == 1; }
   // split: K block
   const int sc[2] = {32, 64};
   best = 1e30f;
@@ -329,19 +437,21 @@ int mixed_autotune(sxl_ctx* c, double* out) {
   }
   c->tc_bk_split = sc[bi];
   if (out) { out[3] = sc[bi]; out[4] = best; }
-  // dual: rows per CTA
-  const int dc[2] = {2, 1};
+  // dual: (rows per CTA, persistent kernel)
+  const int dc[3][2] = {{2, 2}, {1, 2}, {2, 1}};
   best = 1e30f;
   bi = 0;
-  for (int i = 0; i < 2; ++i) {
-    c->tc_mt_dual = dc[i];
+  for (int i = 0; i < 3; ++i) {
+    c->tc_mt_dual = dc[i][0];
+    c->tc_ps_dual = dc[i][1];
     float ms = 0.f;
     SXL_TRY(time_launches(c, [&] { return gemm_tc_dual(c, c->hU, c->hS, c->hS, c->hU, c->hG1, 1.f,
                                                        nullptr, 0.f, 0.f, true); }, reps, &ms));
     if (ms < best) { best = ms; bi = i; }
   }
-  c->tc_mt_dual = dc[bi];
-  if (out) { out[5] = dc[bi]; out[6] = best; }
+  c->tc_mt_dual = dc[bi][0];
+  c->tc_ps_dual = dc[bi][1];
+  if (out) { out[5] = dc[bi][0]; out[6] = best; out[8] = dc[bi][1] == 1; }
   return SXL_OK;
 }
 

@@ -90,6 +90,7 @@ EXPORTS = {
     "sxl_gemm_f64": (_i, [_p, _p, _p, _p, _p, _d, _d, _d, _i]),
     "sxl_autotune": (_i, [_p, _p]),
     "sxl_set_tiles": (_i, [_p, _i, _i, _i, _i]),
+    "sxl_set_product_kernel": (_i, [_p, _i]),
     "sxl_batch_autotune": (_i, [_p, _p]),
     "sxl_mixed_gemm_noalloc": (_i, [_i, _i, _p, _p, _p, _p, _d, _d, _d, _i, _i, _p]),
 }
@@ -360,15 +361,22 @@ class Context:
     def autotune(self):
         """Times the candidate tensor-core tiles on this context and keeps the
         fastest; returns the choice and the times (ms)."""
-        out = np.zeros(7)
+        out = np.zeros(9)
         self._check(self.lib.sxl_autotune(self.h, out.ctypes.data_as(_p)), "sxl_autotune")
         return {"plain_bk": int(out[0]), "plain_rows": 128 * int(out[1]), "plain_ms": out[2],
                 "split_bk": int(out[3]), "split_ms": out[4], "dual_rows": 128 * int(out[5]),
-                "dual_ms": out[6]}
+                "dual_ms": out[6], "plain_persistent": bool(out[7]),
+                "dual_persistent": bool(out[8])}
 
     def set_tiles(self, bk_plain=0, mt_plain=0, bk_split=0, mt_dual=0):
         self._check(self.lib.sxl_set_tiles(self.h, int(bk_plain), int(mt_plain), int(bk_split),
                                            int(mt_dual)), "sxl_set_tiles")
+
+    def set_product_kernel(self, kernel="default"):
+        """Kernel of the plain and dual products: "persistent", "single" or
+        "default"."""
+        code = {"default": 0, "persistent": 1, "single": 2}[kernel]
+        self._check(self.lib.sxl_set_product_kernel(self.h, code), "sxl_set_product_kernel")
 
     def gemm_f64(self, A, B, E=None, alpha=1.0, beta=0.0, gamma=0.0, sym=False):
         """C = alpha A B^T + beta E + gamma I in fp64 (2 x N x N), the fp64
@@ -553,12 +561,12 @@ class Batch:
     def autotune(self):
         """Tile autotuning of every replica (one run per distinct chain
         dimension); returns one dict per tuned dimension."""
-        rep = np.zeros((len(self.contexts), 8))
+        rep = np.zeros((len(self.contexts), 10))
         k = self.lib.sxl_batch_autotune(self.h, rep.ctypes.data_as(_p))
         if k < 0:
             raise SxlError(f"sxl_batch_autotune failed ({k})")
         keys = ("n", "plain_bk", "plain_mt", "plain_ms", "split_bk", "split_ms", "dual_mt",
-                "dual_ms")
+                "dual_ms", "plain_persistent", "dual_persistent")
         return [dict(zip(keys, r.tolist())) for r in rep[:k]]
 
     def step(self, nsteps=1, nthreads=0):

@@ -153,7 +153,8 @@ def test_mixed_padded_chain(sxl, prec, ncell, vac):
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 def test_every_tile_choice_gives_the_product(sxl, prec):
     """Every tile the autotuner may pick (plain: K block 64/32 x 256/128-row
-    tiles; split: K block 32/64; dual: 256/128-row tiles) computes the same
+    tiles or the persistent kernel; split: K block 32/64; dual: 256/128-row
+    tiles or the persistent kernel) computes the same
     product within the form's bound at N = 1152 (ragged 256-column edge), and
     the autotuner returns one of them."""
     w = wl.fe128()
@@ -175,10 +176,55 @@ def test_every_tile_choice_gives_the_product(sxl, prec):
             assert np.abs(C - ref).max() / np.abs(ref).max() < 20 * eps_split, (bk, mt)
             C = ctx.mixed_gemm(A, B, sym=True, split=2).cpu().numpy()
             assert np.abs(C - ref_dual).max() / np.abs(ref_dual).max() < 40 * eps_hi, (bk, mt)
+    ctx.set_product_kernel("persistent")
+    C = ctx.mixed_gemm(A, B, split=False).cpu().numpy()
+    assert np.abs(C - ref).max() / np.abs(ref).max() < 20 * eps_hi
+    C = ctx.mixed_gemm(A, B, sym=True, split=2).cpu().numpy()
+    assert np.abs(C - ref_dual).max() / np.abs(ref_dual).max() < 40 * eps_hi
+    ctx.set_product_kernel("default")
     t = ctx.autotune()
     print(f"{prec} autotune at N = {n}: {t}")
     assert t["plain_bk"] in (32, 64) and t["plain_rows"] in (128, 256)
     assert t["split_bk"] in (32, 64) and t["dual_rows"] in (128, 256)
+    assert isinstance(t["plain_persistent"], bool) and isinstance(t["dual_persistent"], bool)
     with pytest.raises(sxl.SxlError):
         ctx.set_tiles(bk_plain=48)
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("n", [576, 1152, 2304])
+def test_persistent_products_match(sxl, prec, n):
+    """The persistent plain/dual kernel (256 x 128 tiles walked by one CTA
+    per SM, two TMEM accumulator stages) against fp64 and against the
+    single-tile kernel: plain C = A B^T, the symmetric A A^T with E and
+    gamma I, and the dual A B^T + B A^T (symmetric).  N = 576 and 2304 leave
+    partial 256-row tiles and an uneven number of tiles per CTA; each output
+    element sums the same k steps in the same order in both kernels."""
+    ctx = sxl.Context(wl.ModelParams(), n // 9, [60.0, 60.0, 60.0], prec)
+    rng = np.random.default_rng(7)
+    A = np.stack([_sym(rng, n), _sym(rng, n)])
+    B = np.stack([_sym(rng, n), _sym(rng, n)])
+    E = np.stack([_sym(rng, n), _sym(rng, n)])
+    ref = np.einsum("bij,bkj->bik", A, B)
+    ref_sym = 0.5 * np.einsum("bij,bkj->bik", A, A) + 0.25 * E + 0.75 * np.eye(n)
+    ref_dual = ref + np.einsum("bij,bkj->bik", B, A)
+    eps_hi = 2.0 ** -11 if prec == "fp16" else 2.0 ** -8
+    out = {}
+    for kern in ("persistent", "single"):
+        ctx.set_product_kernel(kern)
+        C = ctx.mixed_gemm(A, B, split=False).cpu().numpy()
+        Cs = ctx.mixed_gemm(A, A, E=E, alpha=0.5, beta=0.25, gamma=0.75, sym=True,
+                            split=False).cpu().numpy()
+        Cd = ctx.mixed_gemm(A, B, sym=True, split=2).cpu().numpy()
+        assert np.abs(C - ref).max() / np.abs(ref).max() < 20 * eps_hi, kern
+        assert np.abs(Cs - ref_sym).max() / np.abs(ref_sym).max() < 20 * eps_hi, kern
+        assert np.abs(Cs - Cs.transpose(0, 2, 1)).max() == 0.0, kern
+        assert np.abs(Cd - ref_dual).max() / np.abs(ref_dual).max() < 40 * eps_hi, kern
+        out[kern] = (C, Cs, Cd)
+    for a, b, what in zip(out["persistent"], out["single"], ("plain", "sym", "dual")):
+        d = np.abs(a - b).max()
+        print(f"{prec} n {n} {what}: persistent vs single-tile max diff {d:.3e}")
+        assert d <= 1e-6 * np.abs(b).max(), what
+    ctx.close()
+
