@@ -86,7 +86,11 @@ struct sxl_ctx {
   std::vector<MatH> hAm;  // Y_k - T_{k+1}/2 (response form; hY[k] then holds Y_k + T_{k+1}/2)
   bool apm_ready;         // hY / hAm hold the response operators of the current chain
   MatH hTeff;             // T_nr after a first-order chemical-potential shift
-  MatH hZg, hSh, hHp;     // general model, mixed forms: Z = S^{-1/2}, S^{1/2}, Z H Z
+  // general model, mixed forms: Z with Z^T S Z = I (S^{-1/2} after a cold
+  // start), Z^T, S Z and Z^T S (S^{1/2} after a cold start), Z^T (H - mu0 S) Z;
+  // z_warm: Z holds the last positions' factor (the next one starts from it)
+  MatH hZg, hZt, hSh, hYt, hHp;
+  bool z_warm = false;
   float* fscratch;        // 2 Np^2 fp32 (entropy factorizations, mixed forms)
   bool teff_valid;        // hTeff (not hT[nr]) holds the final density
   double fo_h;            // h = beta dmu / 2 of the mu shift in hTeff (0: none)

@@ -3,18 +3,19 @@
 // tensor-core GEMM of mixed.cu, as (hi, lo) 16-bit pairs on the padded
 // chain dimension Np.
 //
-//   Z = S^{-1/2}, S^{1/2}   coupled Newton-Schulz in split products
-//                           (rebuilt when the positions change)
-//   H_perp = Z H Z          two split products per Hamiltonian
+//   Z with Z^T S Z = I      coupled Newton-Schulz in split products when the
+//                           positions change (S^{-1/2} from a cold start, the
+//                           last Z times M^{-1/2} from a warm one), with Z^T,
+//                           S Z and Z^T S
+//   H_perp = Z^T H Z        two split products per Hamiltonian
 //   U = scale (H_perp - mu I) and the unchanged expansion and mu search
-//   (D S)_ii = (Z D_perp S^{1/2})_ii, D = Z D_perp Z (fp64 copy for forces
-//                           and the band energy)
-//   response                Z dH Z = (X + X^T)/2 with X = S^{1/2} diag(dv) Z,
+//   D = Z D_perp Z^T        fp64 copy for forces, band energy and (D S)_ii
+//   response                Z^T dH Z = (X + X^T)/2 with X = Z^T S diag(dv) Z,
 //                           the chain's derivative from that dense start, the
-//                           last step in full and q_v from (Z dT S^{1/2})_ii
-//   forces                  W = Z D_perp H_perp Z, then the fp64 force kernel
-// The padding orbitals (Np > N) are identity in S, Z and S^{1/2} and sit at
-// the upper spectral bound in U (empty, decoupled states).
+//                           last step in full and q_v from (Z dT Z^T S)_ii
+//   forces                  W = Z D_perp H_perp Z^T, then the fp64 force kernel
+// The padding orbitals (Np > N) are identity in S and Z and sit at the upper
+// spectral bound in U (empty, decoupled states).
 #include "common.cuh"
 
 #include <cmath>
@@ -54,12 +55,13 @@ __device__ __forceinline__ double get_hl(const uint16_t* hi, const uint16_t* lo,
       LAUNCH(KERN<false>, grid, block, 0, (c)->st, __VA_ARGS__);               \
   } while (0)
 
-// The overlap-side products in the bf16 form.  Z, S^{1/2} and every product
-// with them take fp16 pairs (hi + 2^-12 lo, about 2^-23 relative) in both
-// forms: bf16 pairs (about 2^-18) put an error of that size into the metric
-// Z S Z = I and H_perp, and it reaches the Mulliken charges linearly (about
-// 1.3e-4 e at 16 atoms).  Their values are bounded (|S_ij| <= 1, Z and
-// S^{1/2} near I/sqrt(c)), so fp16's range is ample.  The expansion, its
+// The overlap-side products in the bf16 form.  Z, S Z, Z^T S and every
+// product with them take fp16 pairs (hi + 2^-12 lo, about 2^-23 relative) in
+// both forms: bf16 pairs (about 2^-18) put an error of that size into the
+// metric Z^T S Z = I and H_perp, and it reaches the Mulliken charges
+// linearly (about 1.3e-4 e at 16 atoms).  Their values are bounded
+// (|S_ij| <= 1, the factors near S^{-1/2} and S^{1/2} up to a rotation), so
+// fp16's range is ample.  The expansion, its
 // mu search and the response chain keep the form's own pairs; matrices that
 // cross between the two sides are repacked in place.
 struct Fp16Pairs {
@@ -316,37 +318,39 @@ static int repack(sxl_ctx* c, const MatH& X, const MatH& Y, bool to_overlap_side
   return SXL_OK;
 }
 
-// S (fp64) and its split copy; Z = S^{-1/2} and S^{1/2} by the coupled
-// Newton-Schulz iteration on A = S / c (c the Gershgorin bound of S):
+// max |X - I| over the real block of the first spin (synchronizes)
+static int dev_from_eye(sxl_ctx* c, const MatH& X, double* dev) {
+  GDISPATCH(c, k_dev_eye_h, 64, 256, c->N, c->Np, X.hi, X.lo, c->red + 3310);
+  LAUNCH(k_max64, 1, 1, 0, c->st, c->red + 3310, c->red + 3302);
+  CUDA_TRY(c, cudaMemcpyAsync(c->hred, c->red + 3302, sizeof(double), cudaMemcpyDeviceToHost,
+                              c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  *dev = c->hred[0];
+  if (!std::isfinite(*dev)) return sxl_fail(c, SXL_E_NAN, "overlap inverse square root");
+  return SXL_OK;
+}
+
+// Coupled Newton-Schulz iteration for A^{-1/2} and A^{1/2} of a symmetric
+// positive definite A with spectrum in (0, 1] (or near I):
 //   T_k = (3 I - Z_k Y_k)/2, Y_{k+1} = Y_k T_k, Z_{k+1} = T_k Z_k,
-// split symmetric products (the iterates are polynomials in A), stopped one
-// iteration after max |Z_k Y_k - I| < 1e-5 (the split products' floor is
-// near 1e-6); at most 40 iterations, else SXL_E_NO_CONVERGENCE.
-int general_overlap_mixed(sxl_ctx* c, const double* R) {
-  const int N = c->N, Np = c->Np;
-  const size_t npp2 = 2 * (size_t)Np * Np;
-  Fp16Pairs fp16_pairs(c);
-  double cs = 0.0;
-  SXL_TRY(general_overlap_build(c, R, &cs));
-  const MatH ybuf[2] = {c->hX0, c->hG1};
-  const MatH zbuf[2] = {c->hX1, c->hU};
+// from Y_0 = A (in ybuf[0]) and Z_0 = I, in split symmetric products (the
+// iterates are polynomials in A), stopped one iteration after
+// max |Z_k Y_k - I| < 1e-5 (the split products' floor is near 1e-6), checked
+// every iteration from check_from on and every other one before; at most 40
+// iterations, else SXL_E_NO_CONVERGENCE.  *yi, *zi: the final Y and Z.
+static int ns_inv_sqrt(sxl_ctx* c, const MatH ybuf[2], const MatH zbuf[2], int check_from,
+                       int* yi_out, int* zi_out) {
   int yi = 0, zi = 0;
-  GDISPATCH(c, k_split_pad, blocks_for(npp2), 256, N, Np, c->Sb, (size_t)0, 1.0 / cs, 1.0 / cs,
-            ybuf[0].hi, ybuf[0].lo);
   axpy_diag_h(c, zbuf[0], 0.0, ybuf[0], 1.0);  // Z_0 = I
   bool done = false, last = false;
   for (int it = 0; it < 40 && !done; ++it) {
     const MatH& Y = ybuf[yi];
     const MatH& Z = zbuf[zi];
     SXL_TRY(gemm_tc(c, Z, Y, c->hP, 1.f, nullptr, 0.f, 0.f, true, true));  // Z Y
-    if (it % 2 == 1 || it > 8) {
-      GDISPATCH(c, k_dev_eye_h, 64, 256, N, Np, c->hP.hi, c->hP.lo, c->red + 3310);
-      LAUNCH(k_max64, 1, 1, 0, c->st, c->red + 3310, c->red + 3302);
-      CUDA_TRY(c, cudaMemcpyAsync(c->hred, c->red + 3302, sizeof(double), cudaMemcpyDeviceToHost,
-                                  c->st));
-      CUDA_TRY(c, cudaStreamSynchronize(c->st));
-      if (!std::isfinite(c->hred[0])) return sxl_fail(c, SXL_E_NAN, "overlap inverse square root");
-      if (c->hred[0] < 1e-5) last = true;
+    if (it % 2 == 1 || it >= check_from) {
+      double dev = 0.0;
+      SXL_TRY(dev_from_eye(c, c->hP, &dev));
+      if (dev < 1e-5) last = true;
     }
     axpy_diag_h(c, c->hSm, -0.5, c->hP, 1.5);  // T = (3 I - Z Y)/2
     SXL_TRY(gemm_tc(c, Y, c->hSm, ybuf[1 - yi], 1.f, nullptr, 0.f, 0.f, true, true));
@@ -357,8 +361,69 @@ int general_overlap_mixed(sxl_ctx* c, const double* R) {
   }
   if (!done)
     return sxl_fail(c, SXL_E_NO_CONVERGENCE, "overlap inverse square root did not converge");
+  *yi_out = yi;
+  *zi_out = zi;
+  return SXL_OK;
+}
+
+static int copy_pairs(sxl_ctx* c, const MatH& from, const MatH& to) {
+  const size_t bytes = 2 * (size_t)c->Np * c->Np * sizeof(uint16_t);
+  CUDA_TRY(c, cudaMemcpyAsync(to.hi, from.hi, bytes, cudaMemcpyDeviceToDevice, c->st));
+  CUDA_TRY(c, cudaMemcpyAsync(to.lo, from.lo, bytes, cudaMemcpyDeviceToDevice, c->st));
+  return SXL_OK;
+}
+
+// S (fp64) and a factor Z with Z^T S Z = I, with Z^T, S Z and Z^T S, all in
+// split products.
+//  * Cold start (no factor yet, or the last one far from the new S): Z =
+//    S^{-1/2} and S^{1/2} by the coupled iteration on A = S / c (c the
+//    Gershgorin bound of S); then Z = Z^T and S Z = Z^T S = S^{1/2}.
+//  * Warm start from the previous positions' Z0: M = Z0^T S Z0 is near I
+//    (S moves little in one step), and Z = Z0 M^{-1/2} satisfies
+//    Z^T S Z = M^{-1/2} M M^{-1/2} = I exactly, whatever Z0 was.  M^{-1/2} by
+//    the same iteration, which from A = M needs about two iterations instead
+//    of a dozen; Z is no longer symmetric (it is S^{-1/2} times a rotation),
+//    which D = Z f(Z^T H Z) Z^T does not see.
+//    2 products for M, ~6 for M^{-1/2}, 4 for Z, Z^T, S Z, Z^T S: about 12
+//    split products against ~36 for a cold start at 1024 atoms.
+int general_overlap_mixed(sxl_ctx* c, const double* R) {
+  const int N = c->N, Np = c->Np;
+  const size_t npp2 = 2 * (size_t)Np * Np;
+  Fp16Pairs fp16_pairs(c);
+  double cs = 0.0;
+  SXL_TRY(general_overlap_build(c, R, &cs));
+  const MatH ybuf[2] = {c->hX0, c->hG1};
+  const MatH zbuf[2] = {c->hX1, c->hU};
+  int yi = 0, zi = 0;
+  if (c->z_warm) {
+    const MatH& Ss = c->hQ;  // S in pairs (identity on the padding)
+    GDISPATCH(c, k_split_pad, blocks_for(npp2), 256, N, Np, c->Sb, (size_t)0, 1.0, 1.0, Ss.hi,
+              Ss.lo);
+    SXL_TRY(gemm_tc(c, c->hZt, Ss, c->hS, 1.f, nullptr, 0.f, 0.f, false, true));      // Z0^T S
+    SXL_TRY(gemm_tc(c, c->hS, c->hZt, ybuf[0], 1.f, nullptr, 0.f, 0.f, true, true));  // M
+    double dev = 0.0;
+    SXL_TRY(dev_from_eye(c, ybuf[0], &dev));
+    if (dev < 0.25) {
+      SXL_TRY(ns_inv_sqrt(c, ybuf, zbuf, 0, &yi, &zi));
+      const MatH& Mi = zbuf[zi];  // M^{-1/2}
+      SXL_TRY(gemm_tc(c, c->hZg, Mi, c->hP, 1.f, nullptr, 0.f, 0.f, false, true));   // Z0 M^-1/2
+      SXL_TRY(gemm_tc(c, Mi, c->hZg, c->hSm, 1.f, nullptr, 0.f, 0.f, false, true));  // its transpose
+      std::swap(c->hZg, c->hP);
+      std::swap(c->hZt, c->hSm);
+      SXL_TRY(gemm_tc(c, Ss, c->hZt, c->hSh, 1.f, nullptr, 0.f, 0.f, false, true));  // S Z
+      SXL_TRY(gemm_tc(c, c->hZt, Ss, c->hYt, 1.f, nullptr, 0.f, 0.f, false, true));  // Z^T S
+      return SXL_OK;
+    }
+    c->z_warm = false;  // too far from the last factor: start cold
+  }
+  GDISPATCH(c, k_split_pad, blocks_for(npp2), 256, N, Np, c->Sb, (size_t)0, 1.0 / cs, 1.0 / cs,
+            ybuf[0].hi, ybuf[0].lo);
+  SXL_TRY(ns_inv_sqrt(c, ybuf, zbuf, 9, &yi, &zi));
   axpy_diag_h(c, c->hZg, 1.0 / std::sqrt(cs), zbuf[zi], 0.0);
   axpy_diag_h(c, c->hSh, std::sqrt(cs), ybuf[yi], 0.0);
+  SXL_TRY(copy_pairs(c, c->hZg, c->hZt));
+  SXL_TRY(copy_pairs(c, c->hSh, c->hYt));
+  c->z_warm = true;
   return SXL_OK;
 }
 
@@ -380,8 +445,8 @@ int general_hamiltonian_mixed(sxl_ctx* c, const double* n, double* out2_dev) {
   general_hbuild(c, c->H0, c->vorb, c->Mg);
   GDISPATCH(c, k_split_pad, blocks_for(npp2), 256, N, Np, c->Mg, (size_t)N * N, 1.0, 0.0,
             c->hX0.hi, c->hX0.lo, c->Sb, mu0);
-  SXL_TRY(gemm_tc(c, c->hZg, c->hX0, c->hP, 1.f, nullptr, 0.f, 0.f, false, true));  // Z (H - mu0 S)
-  SXL_TRY(gemm_tc(c, c->hP, c->hZg, c->hHp, 1.f, nullptr, 0.f, 0.f, true, true));  // ... Z
+  SXL_TRY(gemm_tc(c, c->hZt, c->hX0, c->hP, 1.f, nullptr, 0.f, 0.f, false, true));  // Z^T (H - mu0 S)
+  SXL_TRY(gemm_tc(c, c->hP, c->hZt, c->hHp, 1.f, nullptr, 0.f, 0.f, true, true));  // ... Z
   const int wpb = 8;
   double* lohi = c->Dg;  // scratch: 4 N doubles
   GDISPATCH(c, k_gersh_h, (2 * N + wpb - 1) / wpb, 32 * wpb, N, Np, c->hHp.hi, c->hHp.lo, mu0,
@@ -397,9 +462,10 @@ void build_u_general_h(sxl_ctx* c, double mu, double scale, double e_pad) {
 }
 
 // After the mu search (T = the final, possibly shifted, T):
-//   D_perp = (I - T)/2, G = Z D_perp, (D S)_ii = (G S^{1/2})_ii, D = G Z (fp64
-//   copy for the forces and the band energy), and the S-weighted
-//   susceptibility diagonal (Z chi_perp S^{1/2})_ii, chi_perp = beta (I - T^2)/4
+//   D_perp = (I - T)/2, G = Z D_perp, D = G Z^T (fp64 copy for the forces,
+//   the band energy and (D S)_ii), and the S-weighted susceptibility diagonal
+//   (Z chi_perp Z^T S)_ii = sum_j (Z chi_perp)_ij (S Z)_ij, chi_perp =
+//   beta (I - T^2)/4
 int general_finish_density_mixed(sxl_ctx* c) {
   const int N = c->N, Np = c->Np;
   const MatH& T = final_T_mixed(c);
@@ -428,8 +494,9 @@ int general_finish_density_mixed(sxl_ctx* c) {
   return SXL_OK;
 }
 
-// Response start: dU = scale Z dH Z with dH = S o (dv 1^T + 1 dv^T)/2, i.e.
-// (X + X^T) scale/2 with X = S^{1/2} diag(dv) Z; then the derivative of the
+// Response start: dU = scale Z^T dH Z with dH = S o (dv 1^T + 1 dv^T)/2 =
+// (diag(dv) S + S diag(dv))/2, i.e. (X + X^T) scale/2 with
+// X = (Z^T S) diag(dv) Z; then the derivative of the
 // chain's start from that dense perturbation (plain products, like every
 // response product):
 //   dS_0 = dU U + U dU,  dQ = -dS_0/3 + 2/15 (dS_0 S + S dS_0),
@@ -440,9 +507,9 @@ int general_response_start_mixed(sxl_ctx* c, const double* v, const MatH& dA) {
   general_potentials(c, v, dv);
   {
     Fp16Pairs fp16_pairs(c);
-    GDISPATCH(c, k_colscale_h, blocks_for(npp2), 256, c->N, c->Np, c->hSh.hi, c->hSh.lo, dv,
+    GDISPATCH(c, k_colscale_h, blocks_for(npp2), 256, c->N, c->Np, c->hYt.hi, c->hYt.lo, dv,
               c->hX0.hi, c->hX0.lo);
-    SXL_TRY(gemm_tc(c, c->hX0, c->hZg, c->hX1, 1.f, nullptr, 0.f, 0.f, false, false));  // X
+    SXL_TRY(gemm_tc(c, c->hX0, c->hZt, c->hX1, 1.f, nullptr, 0.f, 0.f, false, false));  // X
     symcombo_h(c, c->hX0, 0.0, nullptr, 0.5 * c->scale, &c->hX1, 0.0, nullptr, nullptr);  // dU
   }
   SXL_TRY(repack(c, c->hX0, c->hX0, false));
@@ -457,7 +524,7 @@ int general_response_start_mixed(sxl_ctx* c, const double* v, const MatH& dA) {
 }
 
 // Response end from the full dT_n: diag(dT) for the common dmu, a_i =
-// (Z dT S^{1/2})_ii, and q_v per (spin, atom, group)
+// (Z dT Z^T S)_ii = sum_j (Z dT)_ij (S Z)_ij, and q_v per (spin, atom, group)
 int general_response_end_mixed(sxl_ctx* c, const MatH& dT, double* qv, double* dmu_dev) {
   rowstats_h(c, dT, c->diagT + 2 * c->N, nullptr);
   SXL_TRY(repack(c, dT, dT, true));
@@ -470,7 +537,7 @@ int general_response_end_mixed(sxl_ctx* c, const MatH& dT, double* qv, double* d
   return SXL_OK;
 }
 
-// Forces: W^sigma = Z D_perp H_perp Z with D_perp H_perp = (H_perp - T H_perp)/2
+// Forces: W^sigma = Z D_perp H_perp Z^T with D_perp H_perp = (H_perp - T H_perp)/2
 // (split products), copied to fp64, then the fp64 force kernel of the general
 // model.
 int general_forces_mixed(sxl_ctx* c, const double* R, const double* n, double* F, double* erep) {

@@ -86,7 +86,7 @@ static int launch_tc(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a) {
     e1 = ev_get(c);
     CUDA_TRY(c, cudaEventRecord(e0, c->st));
   }
-  k_tc_gemm<BF16, SPLIT, BK, MT, DUAL, CPS><<<grid, 192, Cfg::SMEM, c->st>>>(maps[0], maps[1],
+  k_tc_gemm<BF16, SPLIT, BK, MT, DUAL, CPS><<<grid, TC_THREADS, Cfg::SMEM, c->st>>>(maps[0], maps[1],
                                                                            maps[2], maps[3], a);
   ++g_sxl_launches;
   if (c->time_tc) {
@@ -770,8 +770,10 @@ int sxl_mixed_supported(sxl_ctx* c) {
                 &c->hTeff};
   for (MatH* m : ms) SXL_TRY(halloc(c, m));
   c->hZg.hi = c->hZg.lo = c->hSh.hi = c->hSh.lo = c->hHp.hi = c->hHp.lo = nullptr;
+  c->hZt.hi = c->hZt.lo = c->hYt.hi = c->hYt.lo = nullptr;
+  c->z_warm = false;
   if (c->general) {
-    MatH* gs[] = {&c->hZg, &c->hSh, &c->hHp};
+    MatH* gs[] = {&c->hZg, &c->hZt, &c->hSh, &c->hYt, &c->hHp};
     for (MatH* m : gs) SXL_TRY(halloc(c, m));
   }
   CUDA_TRY(c, cudaMalloc((void**)&c->dup, 2 * (size_t)c->Np * sizeof(double)));
@@ -781,7 +783,7 @@ int sxl_mixed_supported(sxl_ctx* c) {
 
 void sxl_mixed_free(sxl_ctx* c) {
   MatH* ms[] = {&c->hU, &c->hS, &c->hQ, &c->hX0, &c->hX1, &c->hP, &c->hSm, &c->hdTa, &c->hdTb, &c->hG1,
-                &c->hTeff, &c->hZg, &c->hSh, &c->hHp};
+                &c->hTeff, &c->hZg, &c->hZt, &c->hSh, &c->hYt, &c->hHp};
   for (MatH* m : ms) hfree(*m);
   if (c->fscratch) cudaFree(c->fscratch);
   c->fscratch = nullptr;
@@ -1254,9 +1256,9 @@ static int noalloc_run(int n, uint16_t* sc, int* err, const double* A, const dou
   a.err = err;
   dim3 grid(a.ntm * a.ntn, 2);
   if (split)
-    k_tc_gemm<BF16, true, 64><<<grid, 192, TcCfg<true, 64>::SMEM, st>>>(maps[0], maps[1], maps[2], maps[3], a);
+    k_tc_gemm<BF16, true, 64><<<grid, TC_THREADS, TcCfg<true, 64>::SMEM, st>>>(maps[0], maps[1], maps[2], maps[3], a);
   else
-    k_tc_gemm<BF16, false, 64><<<grid, 192, TcCfg<false, 64>::SMEM, st>>>(maps[0], maps[1], maps[2], maps[3], a);
+    k_tc_gemm<BF16, false, 64><<<grid, TC_THREADS, TcCfg<false, 64>::SMEM, st>>>(maps[0], maps[1], maps[2], maps[3], a);
   k_join_f64<BF16><<<g, 256, 0, st>>>(nn, Ch, Cl, C);
   if (cudaGetLastError() != cudaSuccess) return SXL_E_CUDA;
   int flag = 0;

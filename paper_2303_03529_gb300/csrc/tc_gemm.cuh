@@ -2,10 +2,13 @@
 // gamma I on (hi, lo) 16-bit pairs, tcgen05.mma kind::f16 with fp32
 // accumulation in TMEM, operands staged by TMA into swizzled shared memory.
 //
-// Kernel layout (one CTA per 128 x 256 output tile, 192 threads):
-//   warp 0: TMA producer, warp 1: TMEM allocator + MMA issuer (one thread),
-//   warps 2-5: epilogue (TMEM -> registers -> alpha acc + beta E + gamma I ->
-//   hi/lo stores; symmetric outputs also store the mirrored element).
+// Kernel layout (one CTA per 128 x 256 or 256 x 256 output tile, 256 threads):
+//   warp 0: TMA producer, warp 1: TMEM allocator + MMA issuer (one thread);
+//   epilogue (TMEM -> registers -> alpha acc + beta E + gamma I -> hi/lo
+//   stores; symmetric outputs also store the mirrored element) on all eight
+//   warps: warps 2-7 wait for the accumulator, warps 0 and 1 join once their
+//   roles end, and the two warps of each TMEM lane quarter take alternate
+//   32-column chunks.
 // Every wait is bounded (2 s of %globaltimer); on a timeout the CTA records
 // an error, waits (bounded) for its in-flight copies and MMAs, frees TMEM and
 // returns.
@@ -15,6 +18,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#define TC_THREADS 256
 #define TC_BM 128
 #define TC_BN 256
 #define TC_BK 64
@@ -311,7 +315,7 @@ struct TcCfg {
 // concatenated K dimension; the second pair comes in through the tensor maps
 // the split form uses for the lo parts.
 template <bool BF16, bool SPLIT, int BK = TC_BK, int MT = 1, bool DUAL = false, int CPS = 1>
-__global__ void __launch_bounds__(192, CPS)
+__global__ void __launch_bounds__(TC_THREADS, CPS)
     k_tc_gemm(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
               TcArgs g) {
@@ -425,10 +429,14 @@ __global__ void __launch_bounds__(192, CPS)
       s_consumed = kb;
       umma_commit(smem_u32(&acc_bar));
     }
-  } else {
+  }
+  {
     // Epilogue in fp32: acc0 + acc1 2^-12 keeps 24 bits, and w - rn(w) of the
     // hi/lo split is exact in fp32, so no fp64 arithmetic is needed here.
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    // Lanes 1-31 of warps 0 and 1 park here until lane 0 ends its role.
+    __syncwarp();
+    const int q = warp & 3;     // TMEM lane quarter this warp may access
+    const int half = warp >> 2; // the quarter's two warps take alternate chunks
     bool ok = mbar_wait(smem_u32(&acc_bar), 0, &s_abort, true);
     ok = __all_sync(0xffffffffu, ok);
     tc_fence_after();
@@ -442,7 +450,7 @@ __global__ void __launch_bounds__(192, CPS)
       auto chunk_row = [&](int it) { return row0 + (it / (TC_BN / 32)) * TC_BM + q * 32 + lane; };
       auto chunk_col = [&](int it) { return col0 + (it % (TC_BN / 32)) * 32; };
 #pragma unroll 1
-      for (int it = 0; it < NIT; ++it) {
+      for (int it = half; it < NIT; it += 2) {
         uint32_t a0[32], a1[32];
         const uint32_t ta = chunk_addr(it);
         tmem_ld32(ta, a0);

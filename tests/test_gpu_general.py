@@ -209,3 +209,32 @@ def test_general_md_states_every_form(sxl):
         assert rmsmax < 1e-3
         if prec != "fp64":
             assert spread[prec] < spread["fp64"] + 2 * tu
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_general_mixed_warm_factor(sxl, prec):
+    """The overlap factor after a move starts from the previous Z
+    (Z = Z0 M^{-1/2}, M = Z0^T S Z0; no longer symmetric) instead of the
+    cold Newton-Schulz start: at the moved positions the charges and forces
+    of the warm and the cold factor agree to well below the mixed bars, and
+    both meet them against the oracle."""
+    w = wl.fe54_general()
+    p, nat = w.params, w.n_atoms
+    rng = np.random.default_rng(11)
+    R1 = w.R + 0.02 * rng.standard_normal(w.R.shape)
+    warm = sxl.Context(p, nat, w.cell, prec)
+    warm.density(w.R, w.n0)
+    q_w, _ = warm.density(R1, w.n0)
+    F_w, _ = warm.forces(R1, w.n0, energies=False)
+    cold = sxl.Context(p, nat, w.cell, prec)
+    q_c, _ = cold.density(R1, w.n0)
+    F_c, _ = cold.forces(R1, w.n0, energies=False)
+    q_w, F_w, q_c, F_c = (x.cpu().numpy() for x in (q_w, F_w, q_c, F_c))
+    d = general.density(R1, w.cell, w.n0, p)
+    F_o = general.forces(d, R1, w.cell)
+    print(f"{prec}: warm vs cold |dq| {np.abs(q_w - q_c).max():.2e} |dF| {np.abs(F_w - F_c).max():.2e}; "
+          f"warm vs oracle |dq| {np.abs(q_w - d.q).max():.2e} |dF| {np.abs(F_w - F_o).max():.2e}")
+    assert np.abs(q_w - q_c).max() < 5e-5 and np.abs(F_w - F_c).max() < 5e-4
+    assert np.abs(q_w - d.q).max() < 1e-4 and np.abs(F_w - F_o).max() < 1e-3
+    warm.close()
+    cold.close()
