@@ -228,3 +228,28 @@ def test_persistent_products_match(sxl, prec, n):
         assert d <= 1e-6 * np.abs(b).max(), what
     ctx.close()
 
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+def test_tuned_k_block_keeps_the_k_halves(sxl, prec):
+    """The density chain's split products run as two launches over K halves.
+    A context whose split K block differs from the library default (64
+    against 32) must count those halves in its own block width: the same
+    density within the form's noise, and the same tensor-core work (a
+    mis-counted range covered all of K in the first launch and again, as
+    zeros, in the second)."""
+    w = wl.fe128()
+    out = {}
+    for bk in (32, 64):
+        ctx = sxl.Context(w.params, w.n_atoms, w.cell, prec)
+        ctx.set_tiles(bk_split=bk)
+        ctx.enable_gemm_timing(True)
+        q, mu = ctx.density(w.R, w.n0)
+        t = ctx.gemm_timers(reset=True)["split"]
+        out[bk] = (q.cpu().numpy(), mu, t["issued_flops"] / max(t["launches"], 1))
+        ctx.close()
+    dq = np.abs(out[32][0] - out[64][0]).max()
+    print(f"{prec}: K block 32 vs 64: |dq| {dq:.2e}, issued flops per launch "
+          f"{out[32][2]:.4e} / {out[64][2]:.4e}")
+    assert dq < 5e-5
+    assert abs(out[64][2] / out[32][2] - 1.0) < 1e-12
