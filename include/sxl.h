@@ -49,6 +49,10 @@ extern "C" {
 #define SXL_E_NAN             -5  /* a non-finite value was produced            */
 #define SXL_E_STATE           -6  /* call order violated (e.g. no density yet)  */
 #define SXL_E_UNSUPPORTED     -7  /* feature not available on this device       */
+#define SXL_E_TIMEOUT         -8  /* a bounded device wait ran out (the GEMM's
+                                     barrier waits, 2 s; the wait self-test)    */
+#define SXL_E_IO              -9  /* a checkpoint file could not be written or
+                                     read, or does not match the context        */
 
 /* arithmetic of the Fermi-operator expansion and response GEMM chains */
 #define SXL_FP64         0   /* float64 everywhere (parity form)                 */
@@ -190,6 +194,39 @@ int sxl_get_state_host(sxl_ctx* ctx, double* R_host, double* V_host,
  * the state setters this moves the complete MD state through host memory. */
 int sxl_set_derived_host(sxl_ctx* ctx, const double* F_host, const double* Kf_host);
 int sxl_get_derived_host(sxl_ctx* ctx, double* F_host, double* Kf_host);
+
+/* Charges and spins q (2 N_at, or 6 N_at l-resolved; up block then down
+ * block) of the last evaluation at the context state (host array).
+ * SXL_E_STATE before the first evaluation. */
+int sxl_get_charges_host(sxl_ctx* ctx, double* q_host);
+
+/* Checkpoint of the MD state (no counterpart in the paper): R, V, the n
+ * history (newest first), mu and the previous step's mu (the start of the
+ * next mu search), the forces and Kf of the current state, K0 and the step
+ * counter, in one binary file: an 8-byte magic "SXLCKPT1", a fixed header
+ * (version, N_at, length of n, kmax, precision, l_resolved, step counter,
+ * mu, previous mu, payload bytes, FNV-1a 64-bit hash of the payload), then
+ * the arrays as little-endian doubles.  Reading it into a context built
+ * with the same parameters continues the trajectory bit for bit (the
+ * general model's mixed forms rebuild their overlap factor from a cold
+ * start, which agrees to the mixed forms' rounding).  Both calls
+ * synchronize.  SXL_E_STATE when writing before a state is set or
+ * evaluated; SXL_E_IO when the file cannot be written or read, has another
+ * magic or version, another shape, or a payload that does not match its
+ * hash (the context is then left as it was). */
+int sxl_checkpoint_write(sxl_ctx* ctx, const char* path);
+int sxl_checkpoint_read(sxl_ctx* ctx, const char* path);
+/* Steps taken by xlbomd_step and bomd_step since the last sxl_set_state
+ * (restored by sxl_checkpoint_read). */
+long long sxl_md_step(const sxl_ctx* ctx);
+
+/* Self-test of the bounded device wait (no counterpart in the paper): one
+ * warp waits on a device flag that nothing sets, for at most `seconds`
+ * (clamped to [0.001, 2]) of the global timer, then raises the same device
+ * error flag the tensor-core GEMM raises on a barrier timeout.  Returns
+ * SXL_E_TIMEOUT, as a GEMM timeout would, and leaves the context usable (the
+ * flag is cleared when it is reported).  Synchronizes. */
+int sxl_selftest_timeout(sxl_ctx* ctx, double seconds);
 
 /* Stage a9 (Eq. Integration): `nsteps` sXL-BOMD steps from the context
  * state.  stats_host (may be NULL) receives nsteps x 4 doubles

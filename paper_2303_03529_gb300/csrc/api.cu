@@ -272,7 +272,7 @@ static int density_pass(sxl_ctx* c, const double* R, const double* n, double mu_
     if (mixed) {
       int flag = 0;
       SXL_TRY(tc_error_flag(c, &flag));
-      if (flag) return sxl_fail(c, SXL_E_CUDA, "tensor-core GEMM reported a wait timeout");
+      if (flag) return sxl_fail(c, SXL_E_TIMEOUT, "tensor-core GEMM reported a wait timeout");
     }
     double Nmu = c->hred[0], dN = c->hred[1];
     if (dbg)
@@ -378,7 +378,11 @@ static int krylov(sxl_ctx* c, const double* n, int rank, double rel_tol, double*
     krylov_orth(c, k, w, status);
     SXL_TRY(sync_host(c, status, 2));
     if (k == 0) nft = c->hred[1];
-    if (!(c->hred[0] > 1e-12 * nft) || !std::isfinite(c->hred[0])) break;
+    // a non-finite direction means a corrupted K0 or residual: report it
+    // instead of taking the breakdown exit (which would return Kf = 0)
+    if (!std::isfinite(c->hred[0]) || !std::isfinite(nft))
+      return sxl_fail(c, SXL_E_NAN, "non-finite Krylov direction (K0 or the residual)");
+    if (!(c->hred[0] > 1e-12 * nft)) break;
     double* vk = c->Vk + (size_t)k * n2;
     SXL_TRY(response(c, vk, c->qv, c->red + 48));
     vec_axpby(c, n2, c->fv, 1.0, c->qv, -1.0, vk);
@@ -779,6 +783,7 @@ static int set_state(sxl_ctx* c, const double* R, const double* V, const double*
   CUDA_TRY(c, cudaMemcpyAsync(c->nhist, nh, (size_t)K1 * n2 * sizeof(double), kind, c->st));
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   c->hist_head = 0;
+  c->md_step = 0;
   // the same mu as the context holds continues its trajectory: keep the mu
   // history used to extrapolate the next start; any other mu starts afresh
   if (!(mu == c->mu)) c->mu_prev = NAN;
@@ -874,6 +879,7 @@ int xlbomd_step(sxl_ctx* c, int nsteps, double* stats) {
   }
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   c->tm_steps += nsteps;
+  c->md_step += nsteps;
   ev_resolve(c);
   return SXL_OK;
 }
@@ -989,6 +995,7 @@ int bomd_step(sxl_ctx* c, int nsteps, const sxl_scf_opts* opts, double tol, int 
     }
   }
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  c->md_step += nsteps;
   // the derived quantities of an sXL-BOMD step (F, Kf) are not current now
   c->evaluated = false;
   return SXL_OK;
@@ -1005,7 +1012,7 @@ int sxl_mixed_gemm(sxl_ctx* c, const double* A, const double* B, const double* E
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   int flag = 0;
   SXL_TRY(tc_error_flag(c, &flag));
-  if (flag) return sxl_fail(c, SXL_E_CUDA, "tensor-core GEMM reported a wait timeout");
+  if (flag) return sxl_fail(c, SXL_E_TIMEOUT, "tensor-core GEMM reported a wait timeout");
   return SXL_OK;
 }
 
@@ -1020,7 +1027,7 @@ int sxl_autotune(sxl_ctx* c, double* out9) {
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   int flag = 0;
   SXL_TRY(tc_error_flag(c, &flag));
-  if (flag) return sxl_fail(c, SXL_E_CUDA, "tensor-core GEMM reported a wait timeout");
+  if (flag) return sxl_fail(c, SXL_E_TIMEOUT, "tensor-core GEMM reported a wait timeout");
   return SXL_OK;
 }
 
@@ -1107,6 +1114,135 @@ int sxl_get_derived_host(sxl_ctx* c, double* F, double* Kf) {
   CUDA_TRY(c, cudaMemcpyAsync(Kf, c->Kf, c->n2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   return SXL_OK;
+}
+
+int sxl_get_charges_host(sxl_ctx* c, double* q) {
+  if (!c || !q) return SXL_E_ARG;
+  if (!c->evaluated && !c->have_density)
+    return sxl_fail(c, SXL_E_STATE, "no evaluation at the context state yet");
+  CUDA_TRY(c, cudaMemcpyAsync(q, c->q, c->n2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return SXL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint: magic, fixed header, payload of doubles
+//   R (3 N_at), V (3 N_at), n history (kmax+1 vectors, newest first),
+//   F (3 N_at), Kf (n2), K0 (n2 x n2)
+namespace {
+const char kCkptMagic[8] = {'S', 'X', 'L', 'C', 'K', 'P', 'T', '1'};
+struct CkptHeader {
+  uint32_t version, header_bytes;
+  int32_t nat, n2, kmax, precision, l_resolved, reserved;
+  int64_t md_step;
+  double mu, mu_prev;
+  uint64_t payload_bytes, hash;
+};
+uint64_t fnv1a64(const void* data, size_t n) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+size_t ckpt_doubles(const sxl_ctx* c) {
+  const size_t K1 = c->p.kmax + 1, n2 = c->n2;
+  return 9 * (size_t)c->nat + K1 * n2 + n2 + n2 * n2;
+}
+}  // namespace
+
+long long sxl_md_step(const sxl_ctx* c) { return c ? c->md_step : -1; }
+
+int sxl_checkpoint_write(sxl_ctx* c, const char* path) {
+  if (!c || !path) return SXL_E_ARG;
+  if (!c->state_ready) return sxl_fail(c, SXL_E_STATE, "no MD state: call sxl_set_state first");
+  if (!c->evaluated) SXL_TRY(evaluate(c, nullptr));
+  const size_t nat3 = 3 * (size_t)c->nat, n2 = c->n2, K1 = c->p.kmax + 1;
+  std::vector<double> buf(ckpt_doubles(c));
+  double* R = buf.data();
+  double* V = R + nat3;
+  double* nh = V + nat3;
+  double* F = nh + K1 * n2;
+  double* Kf = F + nat3;
+  double* K0 = Kf + n2;
+  double mu = 0.0;
+  SXL_TRY(get_state(c, R, V, nh, &mu, cudaMemcpyDeviceToHost));
+  CUDA_TRY(c, cudaMemcpyAsync(F, c->F, nat3 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(c, cudaMemcpyAsync(Kf, c->Kf, n2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(c, cudaMemcpyAsync(K0, c->K0, n2 * n2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  CkptHeader h{};
+  h.version = 1;
+  h.header_bytes = sizeof(CkptHeader);
+  h.nat = c->nat;
+  h.n2 = c->n2;
+  h.kmax = c->p.kmax;
+  h.precision = c->p.precision;
+  h.l_resolved = c->p.l_resolved;
+  h.md_step = c->md_step;
+  h.mu = mu;
+  h.mu_prev = c->mu_prev;
+  h.payload_bytes = buf.size() * sizeof(double);
+  h.hash = fnv1a64(buf.data(), h.payload_bytes);
+  // written next to the target and renamed over it, so a failed write never
+  // leaves a truncated checkpoint under the target's name
+  const std::string tmp = std::string(path) + ".partial";
+  FILE* f = std::fopen(tmp.c_str(), "wb");
+  if (!f) return sxl_fail(c, SXL_E_IO, "cannot open the checkpoint file for writing");
+  const bool ok = std::fwrite(kCkptMagic, 1, 8, f) == 8 && std::fwrite(&h, sizeof h, 1, f) == 1 &&
+                  std::fwrite(buf.data(), sizeof(double), buf.size(), f) == buf.size();
+  const bool closed = std::fclose(f) == 0;
+  if (!ok || !closed || std::rename(tmp.c_str(), path) != 0) {
+    std::remove(tmp.c_str());
+    return sxl_fail(c, SXL_E_IO, "writing the checkpoint failed");
+  }
+  return SXL_OK;
+}
+
+int sxl_checkpoint_read(sxl_ctx* c, const char* path) {
+  if (!c || !path) return SXL_E_ARG;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return sxl_fail(c, SXL_E_IO, "cannot open the checkpoint file");
+  char magic[8];
+  CkptHeader h{};
+  std::vector<double> buf(ckpt_doubles(c));
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kCkptMagic, 8) == 0 &&
+            std::fread(&h, sizeof h, 1, f) == 1;
+  ok = ok && h.version == 1 && h.header_bytes == sizeof(CkptHeader) && h.nat == c->nat &&
+       h.n2 == c->n2 && h.kmax == c->p.kmax && h.precision == c->p.precision &&
+       h.l_resolved == c->p.l_resolved && h.payload_bytes == buf.size() * sizeof(double);
+  ok = ok && std::fread(buf.data(), sizeof(double), buf.size(), f) == buf.size();
+  std::fclose(f);
+  if (!ok) return sxl_fail(c, SXL_E_IO, "checkpoint header or size does not match the context");
+  if (fnv1a64(buf.data(), h.payload_bytes) != h.hash)
+    return sxl_fail(c, SXL_E_IO, "checkpoint payload does not match its hash");
+  const size_t nat3 = 3 * (size_t)c->nat, n2 = c->n2, K1 = c->p.kmax + 1;
+  const double* R = buf.data();
+  const double* V = R + nat3;
+  const double* nh = V + nat3;
+  const double* F = nh + K1 * n2;
+  const double* Kf = F + nat3;
+  const double* K0 = Kf + n2;
+  SXL_TRY(set_state(c, R, V, nh, h.mu, cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpyAsync(c->F, F, nat3 * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CUDA_TRY(c, cudaMemcpyAsync(c->Kf, Kf, n2 * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CUDA_TRY(c, cudaMemcpyAsync(c->K0, K0, n2 * n2 * sizeof(double), cudaMemcpyHostToDevice, c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  c->mu_prev = h.mu_prev;
+  c->md_step = h.md_step;
+  c->evaluated = true;
+  // the next evaluation rebuilds the model from R, as a fresh context would
+  c->h0_valid = false;
+  c->z_warm = false;
+  c->mu0 = NAN;
+  return SXL_OK;
+}
+
+int sxl_selftest_timeout(sxl_ctx* c, double seconds) {
+  if (!c) return SXL_E_ARG;
+  return selftest_timeout(c, seconds);
 }
 
 int sxl_info(sxl_ctx* c, double* out) {

@@ -91,6 +91,7 @@ struct sxl_ctx {
   // z_warm: Z holds the last positions' factor (the next one starts from it)
   MatH hZg, hZt, hSh, hYt, hHp;
   bool z_warm = false;
+  long long md_step = 0;  // xlbomd_step / bomd_step steps since sxl_set_state
   float* fscratch;        // 2 Np^2 fp32 (entropy factorizations, mixed forms)
   bool teff_valid;        // hTeff (not hT[nr]) holds the final density
   double fo_h;            // h = beta dmu / 2 of the mu shift in hTeff (0: none)
@@ -261,6 +262,7 @@ int dmpt_mixed(sxl_ctx* c, const double* du);
 void dot_h0_t_mixed(sxl_ctx* c, int spin, double* out);
 void density_matrix_mixed(sxl_ctx* c, double* D);
 int tc_error_flag(sxl_ctx* c, int* flag);
+int selftest_timeout(sxl_ctx* c, double seconds);
 int mixed_gemm_test(sxl_ctx* c, const double* A, const double* B, const double* E, double* C,
                     double alpha, double beta, double gamma, int sym, int split);
 int mixed_autotune(sxl_ctx* c, double* out7);

@@ -746,6 +746,20 @@ void hfree(MatH& m) {
   m.hi = m.lo = nullptr;
 }
 
+// The device's wait-timeout flag (created by the first context on the device).
+static int attach_tc_err(sxl_ctx* c, int dev) {
+  if (dev < 0 || dev >= TC_MAX_DEV) return sxl_fail(c, SXL_E_UNSUPPORTED, "device index too large");
+  std::lock_guard<std::mutex> lock(g_tc_err_mutex);
+  if (!g_tc_err[dev]) {
+    int* f = nullptr;
+    CUDA_TRY(c, cudaMalloc((void**)&f, sizeof(int)));
+    CUDA_TRY(c, cudaMemset(f, 0, sizeof(int)));
+    g_tc_err[dev] = f;
+  }
+  c->tc_err = g_tc_err[dev];
+  return SXL_OK;
+}
+
 int sxl_mixed_supported(sxl_ctx* c) {
   // the chain runs on Np = N rounded up to 64 (tile and TMA granularity)
   c->Np = (c->N + 63) / 64 * 64;
@@ -756,16 +770,7 @@ int sxl_mixed_supported(sxl_ctx* c) {
   if (prop.major < 10) return sxl_fail(c, SXL_E_UNSUPPORTED, "tcgen05 needs compute capability 10.x");
   SXL_TRY(get_encode(c));
   if (dev < 0 || dev >= TC_MAX_DEV) return sxl_fail(c, SXL_E_UNSUPPORTED, "device index too large");
-  {
-    std::lock_guard<std::mutex> lock(g_tc_err_mutex);
-    if (!g_tc_err[dev]) {
-      int* f = nullptr;
-      CUDA_TRY(c, cudaMalloc((void**)&f, sizeof(int)));
-      CUDA_TRY(c, cudaMemset(f, 0, sizeof(int)));
-      g_tc_err[dev] = f;
-    }
-    c->tc_err = g_tc_err[dev];
-  }
+  SXL_TRY(attach_tc_err(c, dev));
   MatH* ms[] = {&c->hU, &c->hS, &c->hQ, &c->hX0, &c->hX1, &c->hP, &c->hSm, &c->hdTa, &c->hdTb, &c->hG1,
                 &c->hTeff};
   for (MatH* m : ms) SXL_TRY(halloc(c, m));
@@ -798,11 +803,45 @@ void sxl_mixed_free(sxl_ctx* c) {
   c->apm_ready = false;
 }
 
+// Reads the device's wait-timeout flag and clears it once reported, so the
+// context stays usable after the caller has returned SXL_E_TIMEOUT.
 int tc_error_flag(sxl_ctx* c, int* flag) {
   *flag = 0;
   if (!c->tc_err) return SXL_OK;
   CUDA_TRY(c, cudaMemcpyAsync(flag, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  if (*flag) {
+    CUDA_TRY(c, cudaMemsetAsync(c->tc_err, 0, sizeof(int), c->st));
+    CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  }
+  return SXL_OK;
+}
+
+// One thread waits for *flag != 0 for at most limit_ns of the global timer
+// (and at most 2^24 polls, a few seconds even if the timer stalled), then
+// raises *err as a GEMM barrier timeout does.
+__global__ void k_wait_selftest(const volatile int* flag, unsigned long long limit_ns, int* err) {
+  if (threadIdx.x != 0) return;
+  const uint64_t t0 = gtimer();
+  for (uint32_t i = 0; i < (1u << 24); ++i) {
+    if (*flag) return;
+    if ((i & 255u) == 0 && gtimer() - t0 > limit_ns) break;
+  }
+  atomicExch(err, 1);
+}
+
+int selftest_timeout(sxl_ctx* c, double seconds) {
+  int dev = 0;
+  CUDA_TRY(c, cudaGetDevice(&dev));
+  if (!c->tc_err) SXL_TRY(attach_tc_err(c, dev));
+  const double sec = std::min(2.0, std::max(1e-3, seconds));
+  int* never = reinterpret_cast<int*>(c->red + 4050);  // a flag nothing sets
+  CUDA_TRY(c, cudaMemsetAsync(never, 0, sizeof(int), c->st));
+  LAUNCH(k_wait_selftest, 1, 32, 0, c->st, never, (unsigned long long)(sec * 1e9), c->tc_err);
+  CUDA_TRY(c, cudaGetLastError());
+  int flag = 0;
+  SXL_TRY(tc_error_flag(c, &flag));
+  if (flag) return sxl_fail(c, SXL_E_TIMEOUT, "bounded device wait ran out (self-test)");
   return SXL_OK;
 }
 

@@ -84,6 +84,11 @@ EXPORTS = {
     "sxl_mixed_gemm": (_i, [_p, _p, _p, _p, _p, _d, _d, _d, _i, _i]),
     "sxl_set_derived_host": (_i, [_p, _p, _p]),
     "sxl_get_derived_host": (_i, [_p, _p, _p]),
+    "sxl_get_charges_host": (_i, [_p, _p]),
+    "sxl_checkpoint_write": (_i, [_p, ctypes.c_char_p]),
+    "sxl_checkpoint_read": (_i, [_p, ctypes.c_char_p]),
+    "sxl_md_step": (ctypes.c_longlong, [_p]),
+    "sxl_selftest_timeout": (_i, [_p, _d]),
     "sxl_timers": (_i, [_p, _p, _i]),
     "sxl_enable_gemm_timing": (_i, [_p, _i]),
     "sxl_gemm_timers": (_i, [_p, _p, _i]),
@@ -115,7 +120,16 @@ def load_library(path: str = LIB_PATH):
 
 
 class SxlError(RuntimeError):
-    pass
+    """A library call returned a negative status; .code holds it (SXL_E_*)."""
+
+    def __init__(self, msg, code=None):
+        super().__init__(msg)
+        self.code = code
+
+
+# status codes of include/sxl.h
+E_ARG, E_CUDA, E_NOMEM, E_NO_CONVERGENCE, E_NAN, E_STATE, E_UNSUPPORTED, E_TIMEOUT, E_IO = \
+    -1, -2, -3, -4, -5, -6, -7, -8, -9
 
 
 def make_params(mp, n_atoms: int, cell, precision="fp64", foe_steps=0, foe_u_max=0.0,
@@ -196,7 +210,7 @@ class Context:
     def _check(self, rc, what):
         if rc != 0:
             msg = self.lib.sxl_last_error(self.h).decode()
-            raise SxlError(f"{what} failed ({rc}): {msg}")
+            raise SxlError(f"{what} failed ({rc}): {msg}", rc)
 
     def _dev(self, x):
         import torch
@@ -418,6 +432,30 @@ class Context:
         keys = ("launches", "ms", "issued_flops", "product_flops")
         return {name: dict(zip(keys, out[4 * v:4 * v + 4].tolist()))
                 for v, name in enumerate(("plain", "dual", "split", "fp64"))}
+
+    def charges(self):
+        """q of the last evaluation at the context state (numpy, n2)."""
+        out = np.zeros(self.n2)
+        self._check(self.lib.sxl_get_charges_host(self.h, out.ctypes.data_as(_p)),
+                    "sxl_get_charges_host")
+        return out
+
+    def checkpoint_write(self, path):
+        self._check(self.lib.sxl_checkpoint_write(self.h, os.fsencode(path)),
+                    "sxl_checkpoint_write")
+
+    def checkpoint_read(self, path):
+        self._check(self.lib.sxl_checkpoint_read(self.h, os.fsencode(path)),
+                    "sxl_checkpoint_read")
+
+    def md_step(self):
+        return int(self.lib.sxl_md_step(self.h))
+
+    def selftest_timeout(self, seconds=0.25):
+        """Runs the bounded-wait self-test; raises SxlError with code
+        E_TIMEOUT, as a tensor-core GEMM barrier timeout would."""
+        self._check(self.lib.sxl_selftest_timeout(self.h, float(seconds)),
+                    "sxl_selftest_timeout")
 
     def info(self):
         out = np.zeros(7)
