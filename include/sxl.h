@@ -368,7 +368,8 @@ int sxl_gemm_f64(sxl_ctx* ctx, const double* A_dev, const double* B_dev, const d
  * stream capture.  All calls share the arrays: calls that overlap on the
  * GPU race and must be serialized by the caller.  Synchronizes `stream`.
  * Returns SXL_E_ARG for sizes beyond the maximum or a bad precision,
- * SXL_E_CUDA if a CUDA call fails or the GEMM reports a wait timeout. */
+ * SXL_E_CUDA if a CUDA call fails, SXL_E_TIMEOUT if the GEMM reports a
+ * wait timeout (its flag is reset by the next call). */
 int sxl_mixed_gemm_noalloc(int n, int precision, const double* A_dev, const double* B_dev,
                            const double* E_dev, double* C_dev, double alpha, double beta,
                            double gamma, int sym, int split, void* stream);

@@ -1304,7 +1304,7 @@ static int noalloc_run(int n, uint16_t* sc, int* err, const double* A, const dou
   if (cudaMemcpyAsync(&flag, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return SXL_E_CUDA;
-  return flag ? SXL_E_CUDA : SXL_OK;
+  return flag ? SXL_E_TIMEOUT : SXL_OK;
 }
 
 extern "C" int sxl_mixed_gemm_noalloc(int n, int precision, const double* A, const double* B,
