@@ -336,6 +336,18 @@ int sxl_set_tiles(sxl_ctx* ctx, int bk_plain, int mt_plain, int bk_split, int mt
  * sxl_set_tiles), 0 = library default.  The environment variable SXL_TC_PS
  * (1 or 0) overrides the choice.  SXL_E_ARG for other values. */
 int sxl_set_product_kernel(sxl_ctx* ctx, int kernel);
+/* Diagnostic: the fused plain products of m right-hand sides on the
+ * persistent kernel, as the fused Krylov responses use them (fp64 device
+ * arrays, N x N blocks, 9 N_at a multiple of 64).  For z = 2 j + spin,
+ * j < m: C_z = alpha X_z Y_z^T + beta E_z + gamma I, or with dual != 0
+ * alpha (X_z Y_z^T + Y_z X_z^T) + beta E_z + gamma I.  X holds 2 m blocks
+ * when x_per != 0, else 2 (one per spin, shared by every j); Y likewise; E
+ * (may be NULL) and C hold 2 m.  Each C_z equals the unfused product bit
+ * for bit.  Allocates its working storage; discards any density the
+ * context held.  SXL_E_STATE for an fp64 context. */
+int sxl_mixed_gemm_fused(sxl_ctx* ctx, int m, const double* X_dev, int x_per,
+                         const double* Y_dev, int y_per, const double* E_dev, double* C_dev,
+                         double alpha, double beta, double gamma, int sym, int dual);
 /* Autotunes every replica of a batch; replicas with the same chain
  * dimension share one tuning run.  report_host (may be NULL, 10 doubles per
  * distinct dimension) receives [chain dimension, the 9 values of

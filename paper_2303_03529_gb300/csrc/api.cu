@@ -1016,6 +1016,19 @@ int sxl_mixed_gemm(sxl_ctx* c, const double* A, const double* B, const double* E
   return SXL_OK;
 }
 
+int sxl_mixed_gemm_fused(sxl_ctx* c, int m, const double* X, int x_per, const double* Y,
+                         int y_per, const double* E, double* C, double alpha, double beta,
+                         double gamma, int sym, int dual) {
+  if (!c || !X || !Y || !C || m < 1) return SXL_E_ARG;
+  if (c->p.precision == SXL_FP64) return sxl_fail(c, SXL_E_STATE, "context is fp64");
+  c->have_density = false;
+  SXL_TRY(mixed_gemm_fused_test(c, m, X, x_per, Y, y_per, E, C, alpha, beta, gamma, sym, dual));
+  int flag = 0;
+  SXL_TRY(tc_error_flag(c, &flag));
+  if (flag) return sxl_fail(c, SXL_E_TIMEOUT, "tensor-core GEMM reported a wait timeout");
+  return SXL_OK;
+}
+
 int sxl_autotune(sxl_ctx* c, double* out9) {
   if (!c) return SXL_E_ARG;
   if (c->p.precision == SXL_FP64) return sxl_fail(c, SXL_E_STATE, "context is fp64");

@@ -263,6 +263,12 @@ void dot_h0_t_mixed(sxl_ctx* c, int spin, double* out);
 void density_matrix_mixed(sxl_ctx* c, double* D);
 int tc_error_flag(sxl_ctx* c, int* flag);
 int selftest_timeout(sxl_ctx* c, double seconds);
+int gemm_tc_fused(sxl_ctx* c, int m, const MatH& X, bool x_per, const MatH& Y, bool y_per,
+                  const MatH& C, float alpha, const MatH* E, float beta, float gamma, bool sym,
+                  bool dual);
+int mixed_gemm_fused_test(sxl_ctx* c, int m, const double* X, int x_per, const double* Y,
+                          int y_per, const double* E, double* C, double alpha, double beta,
+                          double gamma, int sym, int dual);
 int mixed_gemm_test(sxl_ctx* c, const double* A, const double* B, const double* E, double* C,
                     double alpha, double beta, double gamma, int sym, int split);
 int mixed_autotune(sxl_ctx* c, double* out7);

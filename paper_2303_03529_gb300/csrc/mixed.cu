@@ -54,9 +54,11 @@ static int get_encode(sxl_ctx* c) {
   return SXL_OK;
 }
 
+// rows: the rows the map spans (0: both spin blocks, 2 n; fused products
+// span 2 m n)
 static int make_map(sxl_ctx* c, CUtensorMap* m, const uint16_t* base, int n, int box_rows,
-                    bool bf16, int bk = TC_BK) {
-  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)(2 * (size_t)n)};
+                    bool bf16, int bk = TC_BK, size_t rows = 0) {
+  cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)(rows ? rows : 2 * (size_t)n)};
   cuuint64_t strides[1] = {(cuuint64_t)n * 2};
   cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
@@ -109,7 +111,8 @@ static int launch_tc(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a) {
 // The persistent plain/dual product (tc_gemm_ps.cuh): one CTA per SM, or
 // one per owned tile when there are fewer.
 template <bool BF16, bool DUAL>
-static int launch_tc_ps(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a) {
+static int launch_tc_ps(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a, int nz = 2,
+                        int zper = 0xF) {
   static std::atomic<bool> attr{false};
   if (!attr.load()) {
     CUDA_TRY(c, cudaFuncSetAttribute(k_tc_gemm_ps<BF16, DUAL>,
@@ -122,11 +125,13 @@ static int launch_tc_ps(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a) {
   CUDA_TRY(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   PsArgs pa;
   pa.g = a;
+  pa.nz = nz;
+  pa.zper = zper;
   pa.tiles = 0;  // tiles of one spin block: all, or those a symmetric product owns
   for (int tm = 0; tm < a.ntm; ++tm)
     pa.tiles += a.sym ? std::max(0, a.ntn - 2 * tm) : a.ntn;
-  const double tiles = pa.tiles;
-  const int grid = std::max(1, std::min(nsm, 2 * pa.tiles));
+  const double tiles = pa.tiles * (nz / 2.0);
+  const int grid = std::max(1, std::min(nsm, nz * pa.tiles));
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->time_tc) {
     e0 = ev_get(c);
@@ -142,7 +147,7 @@ static int launch_tc_ps(sxl_ctx* c, const CUtensorMap* maps, const TcArgs& a) {
     const double kdim = (double)a.nk * PS_BK;
     const double mma = 2.0 * tiles * 2.0 * PS_BM * PS_BN * kdim;
     const double owned = a.sym ? n * (n + 1) / 2 : n * n;
-    const double f32 = 2.0 * 2.0 * owned * kdim;
+    const double f32 = nz * 2.0 * owned * kdim;
     c->ev_pending.push_back({e0, e1, mma, f32, f32, DUAL ? 1 : 0});
   }
   return SXL_OK;
@@ -1162,6 +1167,90 @@ template <bool BF16>
 __global__ void k_join_f64(size_t n, const uint16_t* hi, const uint16_t* lo, double* x) {
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i < n) x[i] = ld_hl_d<BF16>(hi, lo, i);
+}
+
+// Fused plain products for m right-hand sides on the persistent kernel:
+// C_z = alpha X_z Y_z^T + beta E_z + gamma I, z = 2 j + spin over j < m, where
+// X (Y) holds one matrix per z when x_per (y_per), else one per spin shared
+// by every j; C and E hold one per z.  The dual form (dual = true) computes
+// alpha (X_z Y_z^T + Y_z X_z^T) + beta E_z + gamma I over the concatenated K.
+// Each C_z is the product the unfused call would give, bit for bit.
+int gemm_tc_fused(sxl_ctx* c, int m, const MatH& X, bool x_per, const MatH& Y, bool y_per,
+                  const MatH& C, float alpha, const MatH* E, float beta, float gamma, bool sym,
+                  bool dual) {
+  const bool bf16 = pairs_bf16(c);
+  const int n = c->Np;
+  const size_t rows_z = 2 * (size_t)m * n, rows_s = 2 * (size_t)n;
+  CUtensorMap pm[4];
+  SXL_TRY(make_map(c, &pm[0], X.hi, n, PS_BM, bf16, PS_BK, x_per ? rows_z : rows_s));
+  SXL_TRY(make_map(c, &pm[2], Y.hi, n, PS_BN, bf16, PS_BK, y_per ? rows_z : rows_s));
+  int zper = (x_per ? 1 : 0) | (y_per ? 4 : 0);
+  if (dual) {  // A2 = Y, B2 = X
+    SXL_TRY(make_map(c, &pm[1], Y.hi, n, PS_BM, bf16, PS_BK, y_per ? rows_z : rows_s));
+    SXL_TRY(make_map(c, &pm[3], X.hi, n, PS_BN, bf16, PS_BK, x_per ? rows_z : rows_s));
+    zper |= (y_per ? 2 : 0) | (x_per ? 8 : 0);
+  } else {
+    pm[1] = pm[0];
+    pm[3] = pm[2];
+  }
+  TcArgs a;
+  a.n = n;
+  a.ntm = (n + PS_BM - 1) / PS_BM;
+  a.ntn = (n + PS_BN - 1) / PS_BN;
+  a.kb0 = 0;
+  a.nk_half = dual ? n / PS_BK : 0;
+  a.nk = dual ? 2 * a.nk_half : n / PS_BK;
+  a.alpha = alpha;
+  a.beta = beta;
+  a.gamma = gamma;
+  a.Ehi = E ? E->hi : nullptr;
+  a.Elo = E ? E->lo : nullptr;
+  a.Chi = C.hi;
+  a.Clo = C.lo;
+  a.sym = sym ? 1 : 0;
+  a.err = c->tc_err;
+  c->n_gemm++;
+  if (dual)
+    return bf16 ? launch_tc_ps<true, true>(c, pm, a, 2 * m, zper)
+                : launch_tc_ps<false, true>(c, pm, a, 2 * m, zper);
+  return bf16 ? launch_tc_ps<true, false>(c, pm, a, 2 * m, zper)
+              : launch_tc_ps<false, false>(c, pm, a, 2 * m, zper);
+}
+
+// Diagnostic: the fused product on fp64 inputs (X: 2 m or 2 matrices, Y
+// likewise, E and C: 2 m), through temporary pair buffers.
+int mixed_gemm_fused_test(sxl_ctx* c, int m, const double* X, int x_per, const double* Y,
+                          int y_per, const double* E, double* C, double alpha, double beta,
+                          double gamma, int sym, int dual) {
+  if (c->Np != c->N)
+    return sxl_fail(c, SXL_E_ARG, "the diagnostic product needs 9 N_at to be a multiple of 64");
+  const size_t nn = (size_t)c->N * c->N, nz = 2 * (size_t)m;
+  MatH hx{}, hy{}, he{}, hc{};
+  auto alloc = [&](MatH& h, size_t count) -> int {
+    if (cudaMalloc((void**)&h.hi, count * 2) != cudaSuccess ||
+        cudaMalloc((void**)&h.lo, count * 2) != cudaSuccess)
+      return sxl_fail(c, SXL_E_NOMEM, "fused product scratch");
+    return SXL_OK;
+  };
+  int rc = SXL_OK;
+  const size_t cx = (x_per ? nz : 2) * nn, cy = (y_per ? nz : 2) * nn;
+  if ((rc = alloc(hx, cx)) == SXL_OK && (rc = alloc(hy, cy)) == SXL_OK &&
+      (rc = alloc(hc, nz * nn)) == SXL_OK && (!E || (rc = alloc(he, nz * nn)) == SXL_OK)) {
+    DISPATCH(c, k_split_f64, (unsigned)((cx + 255) / 256), 256, 0, cx, X, hx.hi, hx.lo);
+    DISPATCH(c, k_split_f64, (unsigned)((cy + 255) / 256), 256, 0, cy, Y, hy.hi, hy.lo);
+    if (E) DISPATCH(c, k_split_f64, (unsigned)((nz * nn + 255) / 256), 256, 0, nz * nn, E, he.hi, he.lo);
+    rc = gemm_tc_fused(c, m, hx, x_per != 0, hy, y_per != 0, hc, (float)alpha, E ? &he : nullptr,
+                       (float)beta, (float)gamma, sym != 0, dual != 0);
+    if (rc == SXL_OK)
+      DISPATCH(c, k_join_f64, (unsigned)((nz * nn + 255) / 256), 256, 0, nz * nn, hc.hi, hc.lo, C);
+    if (cudaStreamSynchronize(c->st) != cudaSuccess && rc == SXL_OK)
+      rc = sxl_fail(c, SXL_E_CUDA, "fused product");
+  }
+  hfree(hx);
+  hfree(hy);
+  hfree(he);
+  hfree(hc);
+  return rc;
 }
 
 int mixed_gemm_test(sxl_ctx* c, const double* A, const double* B, const double* E, double* C,

@@ -41,6 +41,13 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 struct PsArgs {
   TcArgs g;
   int tiles;
+  // fused products: nz = 2 m matrices (m right-hand sides x 2 spins), bz =
+  // 2 j + spin; bit k of zper set: operand map k (A, A2, B, B2) holds one
+  // matrix per bz (rows bz n), clear: one per spin, shared by the m
+  // right-hand sides (rows (bz & 1) n).  C and E are always per bz.
+  // Plain launches: nz = 2, zper = 0xF.
+  int nz;
+  int zper;
 };
 static_assert(PS_BM == 2 * PS_BN, "the owned-tile count assumes 256 x 128 tiles");
 
@@ -98,7 +105,7 @@ __global__ void __launch_bounds__(192, 1)
   __shared__ int s_issued, s_consumed;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int total = 2 * p.tiles;
+  const int total = p.nz * p.tiles;
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const uint32_t sbase = smem_u32(smem);
 
@@ -147,14 +154,15 @@ __global__ void __launch_bounds__(192, 1)
           const uint32_t fb = smem_u32(&full_bar[s]);
           mbar_expect_tx(fb, Cfg::STAGE_BYTES);
           const uint32_t st = sbase + s * Cfg::STAGE_BYTES;
+          const int zs = bz & 1;
           if (DUAL && kb >= g.nk_half) {
             const int kx = (kb - g.nk_half) * PS_BK;
-            tma_load_2d(st, &mAl, fb, kx, bz * g.n + row0);
-            tma_load_2d(st + Cfg::A_BYTES, &mBl, fb, kx, bz * g.n + col0);
+            tma_load_2d(st, &mAl, fb, kx, ((p.zper & 2) ? bz : zs) * g.n + row0);
+            tma_load_2d(st + Cfg::A_BYTES, &mBl, fb, kx, ((p.zper & 8) ? bz : zs) * g.n + col0);
           } else {
             const int kx = (kb + g.kb0) * PS_BK;
-            tma_load_2d(st, &mAh, fb, kx, bz * g.n + row0);
-            tma_load_2d(st + Cfg::A_BYTES, &mBh, fb, kx, bz * g.n + col0);
+            tma_load_2d(st, &mAh, fb, kx, ((p.zper & 1) ? bz : zs) * g.n + row0);
+            tma_load_2d(st + Cfg::A_BYTES, &mBh, fb, kx, ((p.zper & 4) ? bz : zs) * g.n + col0);
           }
         }
       }

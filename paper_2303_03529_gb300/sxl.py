@@ -96,6 +96,7 @@ EXPORTS = {
     "sxl_autotune": (_i, [_p, _p]),
     "sxl_set_tiles": (_i, [_p, _i, _i, _i, _i]),
     "sxl_set_product_kernel": (_i, [_p, _i]),
+    "sxl_mixed_gemm_fused": (_i, [_p, _i, _p, _i, _p, _i, _p, _p, _d, _d, _d, _i, _i]),
     "sxl_batch_autotune": (_i, [_p, _p]),
     "sxl_mixed_gemm_noalloc": (_i, [_i, _i, _p, _p, _p, _p, _d, _d, _d, _i, _i, _p]),
 }
@@ -370,6 +371,21 @@ class Context:
                                             _ptr(E, nn) if E is not None else None, _ptr(C),
                                             float(alpha), float(beta), float(gamma), int(sym),
                                             int(split)), "sxl_mixed_gemm")
+        return C
+
+    def mixed_gemm_fused(self, X, Y, m, x_per=True, y_per=True, E=None, alpha=1.0, beta=0.0,
+                         gamma=0.0, sym=False, dual=False):
+        """Fused products of m right-hand sides (2 m x N x N result); X and Y
+        hold 2 m blocks when x_per / y_per, else 2 (one per spin)."""
+        X, Y = self._dev(X), self._dev(Y)
+        E = self._dev(E) if E is not None else None
+        C = self._new(2 * m, self.N, self.N)
+        nb = self.N * self.N
+        self._check(self.lib.sxl_mixed_gemm_fused(
+            self.h, int(m), _ptr(X, (2 * m if x_per else 2) * nb), int(x_per),
+            _ptr(Y, (2 * m if y_per else 2) * nb), int(y_per),
+            _ptr(E, 2 * m * nb) if E is not None else None, _ptr(C), float(alpha), float(beta),
+            float(gamma), int(sym), int(dual)), "sxl_mixed_gemm_fused")
         return C
 
     def autotune(self):

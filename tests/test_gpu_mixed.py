@@ -253,3 +253,38 @@ def test_tuned_k_block_keeps_the_k_halves(sxl, prec):
           f"{out[32][2]:.4e} / {out[64][2]:.4e}")
     assert dq < 5e-5
     assert abs(out[64][2] / out[32][2] - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("n", [576, 1152])
+def test_fused_products_match_unfused(sxl, prec, n):
+    """The fused products of m right-hand sides (one persistent launch over
+    2 m matrices, operands shared across the right-hand sides or not) give,
+    block by block, the unfused products bit for bit: the plain form with a
+    shared left operand (the response chain's V = A+ dT), the dual symmetric
+    form with a shared right operand and an E term (the chain's start, dQ)
+    and with a shared left operand (the chain's A- V^T + V A-)."""
+    m = 3
+    ctx = sxl.Context(wl.ModelParams(), n // 9, [60.0, 60.0, 60.0], prec)
+    rng = np.random.default_rng(5)
+    sh = np.stack([_sym(rng, n), _sym(rng, n)])                     # one per spin
+    per = np.stack([_sym(rng, n) for _ in range(2 * m)])            # one per (j, spin)
+    E = np.stack([_sym(rng, n) for _ in range(2 * m)])
+    cases = [
+        dict(X=sh, x_per=False, Y=per, y_per=True, sym=False, dual=False, E=None),
+        dict(X=per, x_per=True, Y=sh, y_per=False, sym=True, dual=True, E=E),
+        dict(X=sh, x_per=False, Y=per, y_per=True, sym=True, dual=True, E=None),
+    ]
+    for k, cs in enumerate(cases):
+        C = ctx.mixed_gemm_fused(cs["X"], cs["Y"], m, cs["x_per"], cs["y_per"], E=cs["E"],
+                                 alpha=0.5, beta=0.25 if cs["E"] is not None else 0.0, gamma=0.75,
+                                 sym=cs["sym"], dual=cs["dual"]).cpu().numpy()
+        for j in range(m):
+            Xj = cs["X"][2 * j:2 * j + 2] if cs["x_per"] else cs["X"]
+            Yj = cs["Y"][2 * j:2 * j + 2] if cs["y_per"] else cs["Y"]
+            Ej = cs["E"][2 * j:2 * j + 2] if cs["E"] is not None else None
+            ref = ctx.mixed_gemm(Xj, Yj, E=Ej, alpha=0.5, beta=0.25 if Ej is not None else 0.0,
+                                 gamma=0.75, sym=cs["sym"], split=2 if cs["dual"] else 0).cpu().numpy()
+            d = np.abs(C[2 * j:2 * j + 2] - ref).max()
+            assert d == 0.0, (k, j, d)
+    ctx.close()
