@@ -87,3 +87,46 @@ def krylov_kernel(dens, K0, rank, f=None, rel_tol=None, breakdown=1e-12):
 def exact_kernel(dens):
     """K = J^{-1} from the full Jacobian (the exact t0 preconditioner)."""
     return np.linalg.inv(dens.jacobian())
+
+
+def krylov_kernel_subspace(dens, K0, candidates, rank, f=None, drop=1e-6):
+    """Recycled-subspace variant of the low-rank kernel (a build choice, not
+    the paper's construction): the directions are not generated one
+    response at a time but taken from a given list.
+
+    directions: f~ = K0 f first, then the candidates in order, each
+                orthogonalized against the directions kept so far (two
+                passes of modified Gram-Schmidt) and kept when its norm
+                after that is above `drop` times its norm before; at most
+                `rank` directions;
+    responses:  f~_v = K0 (q_v - v) for every kept v (independent of one
+                another, so they can be computed together);
+    kernel:     c solves min |F~ c - f~|, K f ~ V c (Eq. mIJacobian with
+                orthonormal V, as in krylov_kernel).
+    With the previous steps' directions as candidates the subspace follows
+    the trajectory and every response of a step is known up front.
+    Returns (Kf, info) like krylov_kernel."""
+    f = dens.residual() if f is None else f
+    ft = K0 @ f
+    nft = np.linalg.norm(ft)
+    V = []
+    for w0 in [ft] + [np.asarray(c, dtype=np.float64) for c in candidates]:
+        if len(V) == rank:
+            break
+        w = np.array(w0, dtype=np.float64)
+        n0 = np.linalg.norm(w)
+        for _ in range(2):
+            for v in V:
+                w = w - (v @ w) * v
+        nw = np.linalg.norm(w)
+        if not nw > drop * n0:
+            continue
+        V.append(w / nw)
+    if not V:
+        return np.zeros_like(f), dict(V=np.zeros((f.size, 0)), FT=np.zeros((f.size, 0)),
+                                      c=np.zeros(0), rel=1.0, rank=0)
+    Vm = np.array(V).T
+    FT = np.array([K0 @ dens.fv(v) for v in V]).T
+    c = np.linalg.lstsq(FT, ft, rcond=None)[0]
+    rel = np.linalg.norm(FT @ c - ft) / max(nft, 1e-300)
+    return Vm @ c, dict(V=Vm, FT=FT, c=c, rel=rel, rank=len(V))

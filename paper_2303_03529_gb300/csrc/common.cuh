@@ -90,6 +90,11 @@ struct sxl_ctx {
   // start), Z^T, S Z and Z^T S (S^{1/2} after a cold start), Z^T (H - mu0 S) Z;
   // z_warm: Z holds the last positions' factor (the next one starts from it)
   MatH hZg, hZt, hSh, hYt, hHp;
+  // fused responses (dmpt_mixed_fused): five batches of fz_cap x 2 Np^2 pairs
+  // and fz_cap padded perturbations
+  MatH fz[5] = {};
+  double* fz_dup = nullptr;
+  int fz_cap = 0;
   bool z_warm = false;
   long long md_step = 0;  // xlbomd_step / bomd_step steps since sxl_set_state
   float* fscratch;        // 2 Np^2 fp32 (entropy factorizations, mixed forms)
@@ -213,6 +218,11 @@ void dot_f64(sxl_ctx* c, long long len, const double* x, const double* y, double
 void small_kernels_density(sxl_ctx* c, double* q, double* stats);
 void small_kernels_response(sxl_ctx* c, double* qv, double* dmu);
 void perturb_du(sxl_ctx* c, const double* dh, double* du);
+// q_v and dmu of a response from the diagonal of its dT (2 N)
+void response_stats_at(sxl_ctx* c, const double* diag, double* qv, double* dmu);
+// responses of m directions at once (orthogonal model, mixed forms): du
+// holds m perturbations (2 N each), diag_out receives m diagonals of dT
+int dmpt_mixed_fused(sxl_ctx* c, int m, const double* du, double* diag_out);
 void gemv_f64(sxl_ctx* c, int n, const double* A, const double* x, double* y, double a,
               const double* z, double b);
 void krylov_orth(sxl_ctx* c, int k, const double* w, double* status);

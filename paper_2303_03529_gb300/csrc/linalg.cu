@@ -335,7 +335,11 @@ __global__ void k_response_stats(int nat, const double* __restrict__ diagdT,
 }
 
 void small_kernels_response(sxl_ctx* c, double* qv, double* dmu) {
-  LAUNCH(k_response_stats, 1, 1024, 0, c->st, c->nat, c->diagT + 2 * c->N, c->chi, qv, dmu);
+  response_stats_at(c, c->diagT + 2 * c->N, qv, dmu);
+}
+
+void response_stats_at(sxl_ctx* c, const double* diag, double* qv, double* dmu) {
+  LAUNCH(k_response_stats, 1, 1024, 0, c->st, c->nat, diag, c->chi, qv, dmu);
 }
 
 // du[s][i] = scale * dh[s][i / 9]

@@ -795,6 +795,10 @@ void sxl_mixed_free(sxl_ctx* c) {
   MatH* ms[] = {&c->hU, &c->hS, &c->hQ, &c->hX0, &c->hX1, &c->hP, &c->hSm, &c->hdTa, &c->hdTb, &c->hG1,
                 &c->hTeff, &c->hZg, &c->hZt, &c->hSh, &c->hYt, &c->hHp};
   for (MatH* m : ms) hfree(*m);
+  for (MatH& f : c->fz) hfree(f);
+  if (c->fz_dup) cudaFree(c->fz_dup);
+  c->fz_dup = nullptr;
+  c->fz_cap = 0;
   if (c->fscratch) cudaFree(c->fscratch);
   c->fscratch = nullptr;
   if (c->dup) cudaFree(c->dup);
@@ -1055,6 +1059,41 @@ int dmpt_mixed_general(sxl_ctx* c, const double* v, double* qv, double* dmu_dev)
   return dmpt_mixed_impl(c, nullptr, v, qv, dmu_dev);
 }
 
+// A+- of every chain step (response sandwich form), once per density; the mu
+// shift after the chain folds into the last pair to first order.
+static bool dmpt_split() {
+  static const int use_split = [] {
+    const char* e = getenv("SXL_DMPT_SPLIT");
+    return (e && atoi(e) == 1) ? 1 : 0;
+  }();
+  return use_split == 1;
+}
+
+static int ensure_apm(sxl_ctx* c) {
+  const int Np = c->Np, nr = c->nr;
+  if (!c->apm_ready) {
+    const size_t pairs = (size_t)Np * Np;
+    for (int k = 0; k < nr; ++k)
+      DISPATCH(c, k_apm_h, (unsigned)((pairs + 255) / 256), 256, 0, pairs, c->hY[k].hi,
+               c->hY[k].lo, c->hT[k + 1].hi, c->hT[k + 1].lo, c->hAm[k].hi, c->hAm[k].lo);
+    // The mu shift after the chain, T_eff = T + h (T^2 - I) + O(h^2), maps
+    // dT -> dT + h (T dT + dT T) = (I + h T) dT (I + h T) + O(h^2): to first
+    // order it folds into the last operators, A+- -> (I + h T_nr) A+-
+    // (products of commuting matrices: symmetric outputs).
+    if (c->fo_h != 0.0) {
+      const float h = (float)c->fo_h;
+      MatH& Ap = c->hY[nr - 1];
+      MatH& Am = c->hAm[nr - 1];
+      SXL_TRY(gemm_tc(c, c->hT[nr], Ap, c->hX0, h, &Ap, 1.f, 0.f, true, false));
+      SXL_TRY(gemm_tc(c, c->hT[nr], Am, c->hX1, h, &Am, 1.f, 0.f, true, false));
+      std::swap(Ap, c->hX0);
+      std::swap(Am, c->hX1);
+    }
+    c->apm_ready = true;
+  }
+  return SXL_OK;
+}
+
 static int dmpt_mixed_impl(sxl_ctx* c, const double* du_real, const double* v_gen, double* qv,
                            double* dmu_dev) {
   const int N = c->N, Np = c->Np, nr = c->nr;
@@ -1063,11 +1102,7 @@ static int dmpt_mixed_impl(sxl_ctx* c, const double* du_real, const double* v_ge
   // about 7e-4 (fp16) / 5e-3 (bf16) against 2e-5 / 1e-4 in the split form,
   // ample for the Krylov kernel, whose output only steers n.  SXL_DMPT_SPLIT=1
   // selects the split form.
-  static const int use_split = [] {
-    const char* e = getenv("SXL_DMPT_SPLIT");
-    return (e && atoi(e) == 1) ? 1 : 0;
-  }();
-  const bool split = use_split == 1;
+  const bool split = dmpt_split();
   const MatH* dA = &c->hdTa;
   const MatH* dB = &c->hdTb;
   if (v_gen) {
@@ -1097,26 +1132,7 @@ static int dmpt_mixed_impl(sxl_ctx* c, const double* du_real, const double* v_ge
   //   dT_{k+1} = A- dT A+ + A+ dT A- = A- V^T + V A-,  V = A+ dT.
   // One full product and one symmetric product over [A- | V][V | A-]^T per
   // step (the three-product form needs half a product more).
-  if (!c->apm_ready) {
-    const size_t pairs = (size_t)Np * Np;
-    for (int k = 0; k < nr; ++k)
-      DISPATCH(c, k_apm_h, (unsigned)((pairs + 255) / 256), 256, 0, pairs, c->hY[k].hi,
-               c->hY[k].lo, c->hT[k + 1].hi, c->hT[k + 1].lo, c->hAm[k].hi, c->hAm[k].lo);
-    // The mu shift after the chain, T_eff = T + h (T^2 - I) + O(h^2), maps
-    // dT -> dT + h (T dT + dT T) = (I + h T) dT (I + h T) + O(h^2): to first
-    // order it folds into the last operators, A+- -> (I + h T_nr) A+-
-    // (products of commuting matrices: symmetric outputs).
-    if (c->fo_h != 0.0) {
-      const float h = (float)c->fo_h;
-      MatH& Ap = c->hY[nr - 1];
-      MatH& Am = c->hAm[nr - 1];
-      SXL_TRY(gemm_tc(c, c->hT[nr], Ap, c->hX0, h, &Ap, 1.f, 0.f, true, false));
-      SXL_TRY(gemm_tc(c, c->hT[nr], Am, c->hX1, h, &Am, 1.f, 0.f, true, false));
-      std::swap(Ap, c->hX0);
-      std::swap(Am, c->hX1);
-    }
-    c->apm_ready = true;
-  }
+  SXL_TRY(ensure_apm(c));
   // Only diag(dT_nr) is needed (q_v): the last step ends in row dots,
   // diag(A- V^T + V A-) = 2 rowdot(A-, V).
   const int wpb = 8;
@@ -1142,6 +1158,68 @@ static int dmpt_mixed_impl(sxl_ctx* c, const double* du_real, const double* v_ge
            c->hAm[nr - 1].lo, c->hG1.hi, c->hG1.lo, 2.0, c->diagT + 2 * N);
   return SXL_OK;
 }
+
+// The responses of m directions at once (orthogonal model): the same steps as
+// dmpt_mixed_impl's orthogonal start and sandwich chain, each product fused
+// over the m right-hand sides (gemm_tc_fused: one persistent launch, the
+// chain's operands shared by all of them), the elementwise steps and the last
+// step's row dots per direction.  Each direction's diag(dT_nr) equals the
+// one dmpt_mixed gives for it alone, bit for bit.
+static int ensure_fused(sxl_ctx* c, int m) {
+  if (m <= c->fz_cap) return SXL_OK;
+  for (MatH& f : c->fz) hfree(f);
+  if (c->fz_dup) cudaFree(c->fz_dup);
+  c->fz_dup = nullptr;
+  c->fz_cap = 0;
+  const size_t count = (size_t)m * 2 * c->Np * c->Np;
+  for (MatH& f : c->fz)
+    if (cudaMalloc((void**)&f.hi, count * 2) != cudaSuccess ||
+        cudaMalloc((void**)&f.lo, count * 2) != cudaSuccess)
+      return sxl_fail(c, SXL_E_NOMEM, "fused response buffers");
+  CUDA_TRY(c, cudaMalloc((void**)&c->fz_dup, (size_t)m * 2 * c->Np * sizeof(double)));
+  c->fz_cap = m;
+  return SXL_OK;
+}
+
+int dmpt_mixed_fused(sxl_ctx* c, int m, const double* du, double* diag_out) {
+  if (c->general || dmpt_split()) return SXL_E_UNSUPPORTED;
+  const int N = c->N, Np = c->Np, nr = c->nr;
+  SXL_TRY(ensure_fused(c, m));
+  const size_t mat = 2 * (size_t)Np * Np;
+  auto view = [&](const MatH& b, int j) { return MatH{b.hi + j * mat, b.lo + j * mat}; };
+  MatH dS = c->fz[0], P = c->fz[1], G = c->fz[2], dA = c->fz[3], dB = c->fz[4];
+  for (int j = 0; j < m; ++j) {
+    double* dup = c->fz_dup + (size_t)j * 2 * Np;
+    LAUNCH(k_pad_vec, (2 * Np + 255) / 256, 256, 0, c->st, N, Np, du + (size_t)j * 2 * N, dup);
+    symcombo_h(c, view(dS, j), 0.0, nullptr, 0.0, nullptr, 1.0, dup, &c->hU);
+  }
+  // dQ = -dS/3 + (2/15)(dS S + S dS); then U dQ
+  SXL_TRY(gemm_tc_fused(c, m, dS, true, c->hS, false, P, (float)(2.0 / 15.0), &dS,
+                        (float)(-1.0 / 3.0), 0.f, true, true));
+  SXL_TRY(gemm_tc_fused(c, m, c->hU, false, P, true, G, 1.f, nullptr, 0.f, 0.f, false, false));
+  for (int j = 0; j < m; ++j)
+    symcombo_h(c, view(dA, j), 0.0, nullptr, 0.5, &(const MatH&)view(G, j), 0.5,
+               c->fz_dup + (size_t)j * 2 * Np, &c->hQ);
+  SXL_TRY(ensure_apm(c));
+  for (int k = 0; k < nr - 1; ++k) {
+    SXL_TRY(gemm_tc_fused(c, m, c->hY[k], false, dA, true, G, 1.f, nullptr, 0.f, 0.f, false,
+                          false));
+    SXL_TRY(gemm_tc_fused(c, m, c->hAm[k], false, G, true, dB, 1.f, nullptr, 0.f, 0.f, true,
+                          true));
+    std::swap(dA, dB);
+  }
+  SXL_TRY(gemm_tc_fused(c, m, c->hY[nr - 1], false, dA, true, G, 1.f, nullptr, 0.f, 0.f, false,
+                        false));
+  const int wpb = 8;
+  for (int j = 0; j < m; ++j) {
+    const MatH g = view(G, j);
+    DISPATCH(c, k_rowdot2_h, (2 * N + wpb - 1) / wpb, 32 * wpb, 0, Np, N, c->hAm[nr - 1].hi,
+             c->hAm[nr - 1].lo, g.hi, g.lo, 2.0, diag_out + (size_t)j * 2 * N);
+  }
+  return SXL_OK;
+}
+
+
 
 void dot_h0_t_mixed(sxl_ctx* c, int spin, double* out) {
   const size_t nn = (size_t)c->Np * c->Np;

@@ -226,3 +226,40 @@ def test_bomd_forces_are_minus_gradient_of_bo_energy():
             return (e_bo(Rp)[0] - e_bo(Rm)[0]) / (2 * h)
         g = (4 * d(1e-3) - d(2e-3)) / 3
         assert abs(g + F[a, c]) < 1e-7, (a, c, g, F[a, c])
+
+
+def test_subspace_kernel_full_basis_is_exact_inverse_jacobian(dens16):
+    """The recycled-subspace variant over a complete candidate basis spans
+    R^{2 N_at}: K f = J^{-1} f (J from unit-direction responses), whatever
+    the candidates' order (f~ comes first, then 31 of the unit vectors fill
+    the space)."""
+    w, d = dens16
+    J = d.jacobian()
+    f = d.residual()
+    rng = np.random.default_rng(1)
+    cands = [np.eye(32)[i] for i in rng.permutation(32)]
+    for K0 in (-np.eye(32), np.diag(-1.0 / (1.0 + np.arange(32) / 10.0))):
+        Kf, info = kernel.krylov_kernel_subspace(d, K0, cands, rank=32)
+        assert info["rank"] == 32
+        np.testing.assert_allclose(Kf, np.linalg.solve(J, f), atol=1e-9)
+        np.testing.assert_allclose(info["V"].T @ info["V"], np.eye(32), atol=1e-12)
+
+
+def test_subspace_kernel_on_the_krylov_span_equals_the_krylov_kernel(dens16):
+    """Candidates that span the paper's rank-m Krylov space give its kernel
+    (the least-squares projection depends on the span only), and candidates
+    already in the span of f~ are dropped."""
+    w, d = dens16
+    K0 = -np.eye(32)
+    Kf_k, info_k = kernel.krylov_kernel(d, K0, rank=5)
+    V = info_k["V"]
+    mix = V @ np.array([[1.0, 0.2, 0.0, 0.3, 0.1], [0.0, 1.0, 0.4, 0.0, 0.2],
+                        [0.5, 0.0, 1.0, 0.1, 0.0], [0.0, 0.3, 0.0, 1.0, 0.6],
+                        [0.1, 0.0, 0.2, 0.0, 1.0]])
+    cands = [mix[:, i] for i in range(5)]
+    Kf_s, info_s = kernel.krylov_kernel_subspace(d, K0, cands, rank=5)
+    assert info_s["rank"] == 5
+    np.testing.assert_allclose(Kf_s, Kf_k, atol=1e-11)
+    ft = K0 @ d.residual()
+    Kf_1, info_1 = kernel.krylov_kernel_subspace(d, K0, [2.0 * ft, -ft], rank=5)
+    assert info_1["rank"] == 1
