@@ -114,6 +114,15 @@ typedef struct {
                                 spin shift sigma J_l s_{I,l} (Eq. nfromP);
                                 0: per atom with J = W / 2                     */
   double J_l[3];             /* l-dependent Stoner parameters (s, p, d), eV    */
+  int    krylov_recycle;     /* xlbomd_step's kernel: 0 = the Krylov
+                                construction of Eq. mIJacobian; 1 = the
+                                recycled-subspace variant (a build choice,
+                                not the paper's): the directions are K0 f
+                                and the previous step's directions,
+                                orthonormalized, so that their responses run
+                                fused (orthogonal model, mixed forms); the
+                                first step after a state is set, and every
+                                SCF, use the Krylov construction           */
 } sxl_params;
 
 /* Create a context bound to the current CUDA device and `stream` (a
@@ -227,6 +236,21 @@ long long sxl_md_step(const sxl_ctx* ctx);
  * SXL_E_TIMEOUT, as a GEMM timeout would, and leaves the context usable (the
  * flag is cleared when it is reported).  Synchronizes. */
 int sxl_selftest_timeout(sxl_ctx* ctx, double seconds);
+
+/* The recycled-subspace variant of the kernel with explicit candidates (no
+ * counterpart in the paper): density at (R_dev, n_dev), then directions
+ * from [K0 f, cand_0, ..., cand_{ncand-1}] (cand_dev: ncand x n2, device;
+ * may be NULL when ncand = 0), each orthogonalized against the kept ones by
+ * two passes of modified Gram-Schmidt and kept when its norm after that
+ * exceeds 1e-6 times its norm before, at most `rank` (<= 32) directions;
+ * their responses (fused when fused != 0 and the context is an orthogonal
+ * mixed one, one by one otherwise), then Kf = V c with c the least squares
+ * of Eq. mIJacobian.  Kf_dev: n2; rel_host (may be NULL): |F~ c - f~| /
+ * |f~|; rank_host (may be NULL): directions kept.  SXL_E_NAN for a
+ * non-finite direction. */
+int krylov_kernel_subspace(sxl_ctx* ctx, const double* R_dev, const double* n_dev,
+                           const double* cand_dev, int ncand, int rank, int fused,
+                           double* Kf_dev, double* rel_host, int* rank_host);
 
 /* Stage a9 (Eq. Integration): `nsteps` sXL-BOMD steps from the context
  * state.  stats_host (may be NULL) receives nsteps x 4 doubles

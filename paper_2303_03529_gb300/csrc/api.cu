@@ -410,6 +410,90 @@ static int krylov(sxl_ctx* c, const double* n, int rank, double rel_tol, double*
   return SXL_OK;
 }
 
+// The recycled-subspace variant of the kernel (a build choice, not the
+// paper's construction): directions from [K0 f, cand_0, ...] instead of one
+// response at a time, so that all their responses are known up front and,
+// in the orthogonal model's mixed forms, run as one fused chain.  Each
+// candidate is orthogonalized against the kept directions (two passes of
+// modified Gram-Schmidt, k_krylov_orth) and kept when its norm after that
+// exceeds 1e-6 times its norm before; at most `rank` directions.  cand may
+// alias c->Vrec (it is copied before Vk is written).
+static int krylov_subspace(sxl_ctx* c, const double* n, const double* cand, int ncand,
+                           int rank, bool fused, double* rel_out, int* rank_out) {
+  const int n2 = c->n2, N = c->N;
+  if (!c->rk_buf) {
+    // candidates (32 x n2), perturbations and diagonals (32 x 2 N each), q_v (32 x n2)
+    const size_t len = 32 * (size_t)n2 * 2 + 32 * 4 * (size_t)N + 64;
+    CUDA_TRY(c, cudaMalloc((void**)&c->rk_buf, len * sizeof(double)));
+  }
+  double* cbuf = c->rk_buf;
+  double* du_all = cbuf + 32 * (size_t)n2;
+  double* diag_all = du_all + 32 * 2 * (size_t)N;
+  double* qv_all = diag_all + 32 * 2 * (size_t)N;
+  double* dmu_all = qv_all + 32 * (size_t)n2;
+  ncand = std::min(ncand, 31);
+  if (ncand > 0)
+    CUDA_TRY(c, cudaMemcpyAsync(cbuf, cand, (size_t)ncand * n2 * sizeof(double),
+                                cudaMemcpyDeviceToDevice, c->st));
+  vec_axpby(c, n2, c->fres, 1.0, c->q, -1.0, n);
+  gemv_f64(c, n2, c->K0, c->fres, c->ftil, 1.0, nullptr, 0.0);
+  double* status = c->red + 32;
+  double* lsq = c->red + 40;
+  int k = 0;
+  for (int i = 0; i <= ncand && k < rank; ++i) {
+    const double* w = i == 0 ? c->ftil : cbuf + (size_t)(i - 1) * n2;
+    krylov_orth(c, k, w, status);
+    SXL_TRY(sync_host(c, status, 2));
+    if (!std::isfinite(c->hred[0]) || !std::isfinite(c->hred[1]))
+      return sxl_fail(c, SXL_E_NAN, "non-finite Krylov direction (K0, the residual or a candidate)");
+    if (c->hred[0] > 1e-6 * c->hred[1]) ++k;
+  }
+  double rel = 1.0;
+  if (k == 0) {
+    CUDA_TRY(c, cudaMemsetAsync(c->Kf, 0, n2 * sizeof(double), c->st));
+  } else {
+    const bool mixed = c->p.precision != SXL_FP64;
+    bool done = false;
+    if (fused && mixed && !c->general) {
+      for (int j = 0; j < k; ++j) {
+        launch_spin_shift(c, c->Vk + (size_t)j * n2, c->dh);
+        perturb_du(c, c->dh, du_all + (size_t)j * 2 * N);
+      }
+      const int rc = dmpt_mixed_fused(c, k, du_all, diag_all);
+      if (rc == SXL_OK) {
+        for (int j = 0; j < k; ++j)
+          response_stats_at(c, diag_all + (size_t)j * 2 * N, qv_all + (size_t)j * n2, dmu_all + j);
+        done = true;
+      } else if (rc != SXL_E_UNSUPPORTED) {
+        return rc;
+      }
+    }
+    if (!done)
+      for (int j = 0; j < k; ++j)
+        SXL_TRY(response(c, c->Vk + (size_t)j * n2, qv_all + (size_t)j * n2, dmu_all + j));
+    for (int j = 0; j < k; ++j) {
+      vec_axpby(c, n2, c->fv, 1.0, qv_all + (size_t)j * n2, -1.0, c->Vk + (size_t)j * n2);
+      gemv_f64(c, n2, c->K0, c->fv, c->FTk + (size_t)j * n2, 1.0, nullptr, 0.0);
+    }
+    krylov_lsq(c, k, lsq);
+    SXL_TRY(sync_host(c, lsq, 1));
+    rel = c->hred[0];
+  }
+  if (rel_out) *rel_out = rel;
+  if (rank_out) *rank_out = k;
+  return SXL_OK;
+}
+
+// The directions of the last kernel, kept for the next step's recycled kernel.
+static int keep_subspace(sxl_ctx* c, int k) {
+  if (!c->Vrec) CUDA_TRY(c, cudaMalloc((void**)&c->Vrec, 32 * (size_t)c->n2 * sizeof(double)));
+  if (k > 0)
+    CUDA_TRY(c, cudaMemcpyAsync(c->Vrec, c->Vk, (size_t)k * c->n2 * sizeof(double),
+                                cudaMemcpyDeviceToDevice, c->st));
+  c->nrec = k;
+  return SXL_OK;
+}
+
 __global__ void k_energy_band(int N, const double* __restrict__ H0, double d0s, double d0p,
                               double d0d, const double* dots, double* out) {
   __shared__ double sm[1024];
@@ -634,7 +718,7 @@ int sxl_destroy(sxl_ctx* c) {
                     c->gamma_m, c->H0, c->h0abs, c->shift, c->U, c->S, c->Q, c->X0, c->X1, c->P,
                     c->Sm, c->dTa, c->dTb, c->G1, c->diagT, c->rowsq, c->chi, c->du, c->dh,
                     c->red, c->K0, c->Vk, c->FTk, c->ftil, c->cvec, c->qv, c->fv, c->wvec, c->Jm,
-                    c->Jinv};
+                    c->Jinv, c->Vrec, c->rk_buf};
   for (double* p : ptrs)
     if (p) cudaFree(p);
   if (c->H0f) cudaFree(c->H0f);
@@ -765,6 +849,19 @@ int krylov_kernel_apply(sxl_ctx* c, const double* R, const double* n, int rank, 
   return SXL_OK;
 }
 
+int krylov_kernel_subspace(sxl_ctx* c, const double* R, const double* n, const double* cand,
+                           int ncand, int rank, int fused, double* Kf, double* rel, int* rank_out) {
+  if (!c || !R || !n || !Kf || rank < 1 || rank > 32 || ncand < 0 || (ncand > 0 && !cand))
+    return SXL_E_ARG;
+  double g = c->have_density ? c->mu : NAN;
+  c->have_density = false;
+  SXL_TRY(density(c, R, n, g));
+  SXL_TRY(krylov_subspace(c, n, cand, ncand, rank, fused != 0, rel, rank_out));
+  CUDA_TRY(c, cudaMemcpyAsync(Kf, c->Kf, c->n2 * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
+  CUDA_TRY(c, cudaStreamSynchronize(c->st));
+  return SXL_OK;
+}
+
 int forces(sxl_ctx* c, const double* R, const double* n, double* F, double* en) {
   if (!c || !R || !n || !F) return SXL_E_ARG;
   double g = c->have_density ? c->mu : NAN;
@@ -784,6 +881,7 @@ static int set_state(sxl_ctx* c, const double* R, const double* V, const double*
   CUDA_TRY(c, cudaStreamSynchronize(c->st));
   c->hist_head = 0;
   c->md_step = 0;
+  c->nrec = 0;  // the recycled kernel starts from the Krylov construction
   // the same mu as the context holds continues its trajectory: keep the mu
   // history used to extrapolate the next start; any other mu starts afresh
   if (!(mu == c->mu)) c->mu_prev = NAN;
@@ -840,7 +938,12 @@ static int evaluate(sxl_ctx* c, double* en) {
   SXL_TRY(eval_forces(c, c->R, n, c->F, en));
   cudaEvent_t f1 = phase_mark(c), k0 = phase_mark(c);
   int rank = 0;
-  SXL_TRY(krylov(c, n, c->p.krylov_rank, 0.0, c->Kf, nullptr, &rank));
+  if (c->p.krylov_recycle && c->nrec > 0) {
+    SXL_TRY(krylov_subspace(c, n, c->Vrec, c->nrec, c->p.krylov_rank, true, nullptr, &rank));
+  } else {
+    SXL_TRY(krylov(c, n, c->p.krylov_rank, 0.0, c->Kf, nullptr, &rank));
+  }
+  if (c->p.krylov_recycle) SXL_TRY(keep_subspace(c, rank));
   cudaEvent_t k1 = phase_mark(c);
   c->ph_pending.push_back({d0, d1, 0.0, 0.0, 0.0, -1});
   c->ph_pending.push_back({f0, f1, 1.0, 0.0, 0.0, -1});

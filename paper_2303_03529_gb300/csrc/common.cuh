@@ -97,6 +97,11 @@ struct sxl_ctx {
   int fz_cap = 0;
   bool z_warm = false;
   long long md_step = 0;  // xlbomd_step / bomd_step steps since sxl_set_state
+  // recycled-subspace kernel: the last directions (32 x n2) and their count;
+  // scratch for candidates, fused perturbations, diagonals and responses
+  double* Vrec = nullptr;
+  int nrec = 0;
+  double* rk_buf = nullptr;
   float* fscratch;        // 2 Np^2 fp32 (entropy factorizations, mixed forms)
   bool teff_valid;        // hTeff (not hT[nr]) holds the final density
   double fo_h;            // h = beta dmu / 2 of the mu shift in hTeff (0: none)

@@ -1197,9 +1197,11 @@ int dmpt_mixed_fused(sxl_ctx* c, int m, const double* du, double* diag_out) {
   SXL_TRY(gemm_tc_fused(c, m, dS, true, c->hS, false, P, (float)(2.0 / 15.0), &dS,
                         (float)(-1.0 / 3.0), 0.f, true, true));
   SXL_TRY(gemm_tc_fused(c, m, c->hU, false, P, true, G, 1.f, nullptr, 0.f, 0.f, false, false));
-  for (int j = 0; j < m; ++j)
-    symcombo_h(c, view(dA, j), 0.0, nullptr, 0.5, &(const MatH&)view(G, j), 0.5,
-               c->fz_dup + (size_t)j * 2 * Np, &c->hQ);
+  for (int j = 0; j < m; ++j) {
+    const MatH gj = view(G, j);
+    symcombo_h(c, view(dA, j), 0.0, nullptr, 0.5, &gj, 0.5, c->fz_dup + (size_t)j * 2 * Np,
+               &c->hQ);
+  }
   SXL_TRY(ensure_apm(c));
   for (int k = 0; k < nr - 1; ++k) {
     SXL_TRY(gemm_tc_fused(c, m, c->hY[k], false, dA, true, G, 1.f, nullptr, 0.f, 0.f, false,

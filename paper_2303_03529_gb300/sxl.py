@@ -43,6 +43,7 @@ class Params(ctypes.Structure):
         ("precision", _i), ("foe_steps", _i), ("foe_u_max", _d),
         ("mu_max_iter", _i), ("mu_tol", _d), ("scf_keep_k0", _i),
         ("S0", _d * 10), ("s_decay", _d), ("l_resolved", _i), ("J_l", _d * 3),
+        ("krylov_recycle", _i),
     ]
 
 
@@ -89,6 +90,7 @@ EXPORTS = {
     "sxl_checkpoint_read": (_i, [_p, ctypes.c_char_p]),
     "sxl_md_step": (ctypes.c_longlong, [_p]),
     "sxl_selftest_timeout": (_i, [_p, _d]),
+    "krylov_kernel_subspace": (_i, [_p, _p, _p, _p, _i, _i, _i, _p, _p, _p]),
     "sxl_timers": (_i, [_p, _p, _i]),
     "sxl_enable_gemm_timing": (_i, [_p, _i]),
     "sxl_gemm_timers": (_i, [_p, _p, _i]),
@@ -134,7 +136,7 @@ E_ARG, E_CUDA, E_NOMEM, E_NO_CONVERGENCE, E_NAN, E_STATE, E_UNSUPPORTED, E_TIMEO
 
 
 def make_params(mp, n_atoms: int, cell, precision="fp64", foe_steps=0, foe_u_max=0.0,
-                mu_tol=0.0, mu_max_iter=0, scf_keep_k0=0) -> Params:
+                mu_tol=0.0, mu_max_iter=0, scf_keep_k0=0, krylov_recycle=0) -> Params:
     """Params from a workload.ModelParams-like object."""
     p = Params()
     p.n_atoms = int(n_atoms)
@@ -161,6 +163,7 @@ def make_params(mp, n_atoms: int, cell, precision="fp64", foe_steps=0, foe_u_max
     p.s_decay = float(getattr(mp, "s_decay", mp.q_decay))
     p.l_resolved = int(bool(getattr(mp, "l_resolved", False)))
     p.J_l[:] = [float(x) for x in getattr(mp, "J_l", (0.5 * mp.W,) * 3)]
+    p.krylov_recycle = int(krylov_recycle)
     return p
 
 
@@ -448,6 +451,20 @@ class Context:
         keys = ("launches", "ms", "issued_flops", "product_flops")
         return {name: dict(zip(keys, out[4 * v:4 * v + 4].tolist()))
                 for v, name in enumerate(("plain", "dual", "split", "fp64"))}
+
+    def krylov_subspace(self, R, n, cand, rank, fused=True):
+        """The recycled-subspace kernel at (R, n) with explicit candidate
+        directions (k x n2, or None); returns (Kf, rel, directions kept)."""
+        R, n = self._dev(R), self._dev(n)
+        cand = self._dev(cand) if cand is not None and len(cand) else None
+        k = 0 if cand is None else int(cand.shape[0])
+        Kf = self._new(self.n2)
+        rel, rk = _d(0.0), _i(0)
+        self._check(self.lib.krylov_kernel_subspace(
+            self.h, _ptr(R, 3 * self.nat), _ptr(n, self.n2),
+            _ptr(cand, k * self.n2) if cand is not None else None, k, int(rank), int(fused),
+            _ptr(Kf), ctypes.byref(rel), ctypes.byref(rk)), "krylov_kernel_subspace")
+        return Kf, rel.value, rk.value
 
     def charges(self):
         """q of the last evaluation at the context state (numpy, n2)."""
