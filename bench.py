@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fe1024")
     ap.add_argument("--precision", default="fp16", choices=["fp16", "bf16", "fp64"])
+    ap.add_argument("--krylov", default="krylov", choices=["krylov", "recycled"],
+                    help="xlbomd_step's kernel: the Krylov construction of Eq. mIJacobian, or "
+                         "the recycled-subspace variant with fused responses")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--gemm-only", action="store_true",
@@ -204,7 +207,7 @@ def replica_throughput(steps_per_rank: int, world: int, max_seconds: float) -> f
     return world * steps_per_rank / max_seconds
 
 
-def prepare_state(sxl, w, precision, local):
+def prepare_state(sxl, w, precision, local, krylov_recycle=0):
     """Initial MD state: SCF from n = 0 with the Krylov kernel mixer and
     K0 = -I (outside the timed region), all history slots = n*.  The general
     model's mixer starts at the first iteration (its linear-mixing phase
@@ -213,7 +216,8 @@ def prepare_state(sxl, w, precision, local):
     import torch
     p = w.params
     general = bool(getattr(p, "l_resolved", False))
-    ctx = sxl.Context(p, w.n_atoms, w.cell, precision, scf_keep_k0=1)
+    ctx = sxl.Context(p, w.n_atoms, w.cell, precision, scf_keep_k0=1,
+                      krylov_recycle=krylov_recycle)
     n0 = np.zeros(ctx.n2)
     t0 = time.time()
     if general:
@@ -336,7 +340,8 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
     w = workload.WORKLOADS[args.workload]()
-    ctx, setup = prepare_state(sxl, w, args.precision, local)
+    ctx, setup = prepare_state(sxl, w, args.precision, local,
+                               1 if args.krylov == "recycled" else 0)
     stream = ctx.stream
 
     def barrier():
@@ -426,6 +431,9 @@ def run_ours(args):
                    "precision": args.precision, "parallelism": f"replicas x{ws}",
                    "l2": "inputs larger than L2 (each chain matrix 2 x 9216^2 x 4 B = 680 MB)",
                    "k0": "-I (scaled delta kernel)", "init": setup,
+                   "krylov": ("recycled subspace, fused responses (a variant, not the paper's "
+                              "construction)" if args.krylov == "recycled"
+                              else "Krylov construction (Eq. mIJacobian)"),
                    "timed_step": "full xlbomd_step; the shadow energy (entropy included) is "
                                  "evaluated only in the untimed statistics step"},
         "krylov_ranks_per_s": round(ranks_per_s, 4) if ranks_per_s else None,

@@ -243,8 +243,10 @@ int sxl_selftest_timeout(sxl_ctx* ctx, double seconds);
  * may be NULL when ncand = 0), each orthogonalized against the kept ones by
  * two passes of modified Gram-Schmidt and kept when its norm after that
  * exceeds 1e-6 times its norm before, at most `rank` (<= 32) directions;
- * their responses (fused when fused != 0 and the context is an orthogonal
- * mixed one, one by one otherwise), then Kf = V c with c the least squares
+ * their responses (fused when fused != 0, the context is an orthogonal
+ * mixed one and its chain dimension is at most 4608, where the fused
+ * products' persistent kernel is the faster one; one by one otherwise),
+ * then Kf = V c with c the least squares
  * of Eq. mIJacobian.  Kf_dev: n2; rel_host (may be NULL): |F~ c - f~| /
  * |f~|; rank_host (may be NULL): directions kept.  SXL_E_NAN for a
  * non-finite direction. */

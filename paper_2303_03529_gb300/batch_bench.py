@@ -35,9 +35,12 @@ def main():
     ap.add_argument("--count", type=int, default=48)
     ap.add_argument("--autotune", action="store_true",
                     help="tile autotuning of every replica before the run")
+    ap.add_argument("--recycle", action="store_true",
+                    help="the recycled-subspace kernel with fused responses (a variant, "
+                         "not the paper's Krylov construction)")
     args = ap.parse_args()
     reps = workload.replica_set(args.count)
-    b = sxl.Batch(reps, "fp16")
+    b = sxl.Batch(reps, "fp16", krylov_recycle=1 if args.recycle else 0)
     tuned = b.autotune() if args.autotune else None
     for ctx, w in zip(b.contexts, reps):
         nat = w.R.shape[0]
@@ -67,6 +70,7 @@ def main():
         "gemm_launches": int(sum(t["tc_launches"] for t in tm)),
         "precision": "fp16", "data": "synthetic (workload.replica_set, seeded)",
         "tiles": "autotuned per chain dimension" if tuned else "library defaults",
+        "krylov": "recycled subspace, fused responses" if args.recycle else "Krylov construction",
         "tuned": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in t.items()}
                   for t in tuned] if tuned else None,
     }

@@ -454,7 +454,10 @@ static int krylov_subspace(sxl_ctx* c, const double* n, const double* cand, int 
   } else {
     const bool mixed = c->p.precision != SXL_FP64;
     bool done = false;
-    if (fused && mixed && !c->general) {
+    // fused products run on the persistent kernel, which is faster than the
+    // single-tile one up to n = 4608 and slower above (measured): larger
+    // chains take their responses one by one
+    if (fused && mixed && !c->general && c->Np <= 4608) {
       for (int j = 0; j < k; ++j) {
         launch_spin_shift(c, c->Vk + (size_t)j * n2, c->dh);
         perturb_du(c, c->dh, du_all + (size_t)j * 2 * N);
