@@ -218,7 +218,8 @@ int sxl_get_charges_host(sxl_ctx* ctx, double* q_host);
  * the arrays as little-endian doubles.  Reading it into a context built
  * with the same parameters continues the trajectory bit for bit (the
  * general model's mixed forms rebuild their overlap factor from a cold
- * start, which agrees to the mixed forms' rounding).  Both calls
+ * start, which agrees to the mixed forms' rounding, and the recycled
+ * kernel restarts from the Krylov construction).  Both calls
  * synchronize.  SXL_E_STATE when writing before a state is set or
  * evaluated; SXL_E_IO when the file cannot be written or read, has another
  * magic or version, another shape, or a payload that does not match its
