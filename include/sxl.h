@@ -81,7 +81,7 @@ typedef struct {
   double d0_s, d0_p, d0_d;   /* neutral-atom occupation per spin and orbital   */
   double rep_A, rep_b;       /* pair repulsion A exp(-b (r - r0)) s(r)         */
   double mass_amu, dt_fs;
-  int    krylov_rank;        /* m of Eq. mIJacobian                            */
+  int    krylov_rank;        /* m of Eq. mIJacobian, 1..32                     */
   int    kmax;               /* dissipation history length, c has kmax+1 terms */
   double kappa, alpha;
   double c[10];

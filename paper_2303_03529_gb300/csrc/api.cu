@@ -644,6 +644,8 @@ int sxl_create(const sxl_params* prm, void* stream, sxl_ctx** out) {
   if (general && !(p.s_decay > 0)) return SXL_E_ARG;
   for (int i = 0; i < 3; ++i)
     if (!std::isfinite(p.J_l[i])) return SXL_E_ARG;
+  if (p.krylov_recycle != 0 && p.krylov_recycle != 1) return SXL_E_ARG;
+  if (p.krylov_rank < 1 || p.krylov_rank > 32) return SXL_E_ARG;
   sxl_ctx* c = new sxl_ctx();
   c->p = p;
   c->st = (cudaStream_t)stream;
