@@ -1261,7 +1261,7 @@ struct CkptHeader {
 };
 uint64_t fnv1a64(const void* data, size_t n) {
   const unsigned char* p = static_cast<const unsigned char*>(data);
-  uint64_t h = 1469598103934665603ull;
+  uint64_t h = 14695981039346656037ull;  // FNV-1a 64-bit offset basis
   for (size_t i = 0; i < n; ++i) {
     h ^= p[i];
     h *= 1099511628211ull;

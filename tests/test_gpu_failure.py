@@ -149,3 +149,31 @@ def test_jsonl_log_of_a_run(sxl, tmp_path):
         assert math.isfinite(r["E_tot_per_atom"]) and r["T"] > 0 and r["rms_q_minus_n"] < 1e-2
         assert math.isfinite(r["m_total"]) and r["wall_s_per_step"] > 0
     ctx.close()
+
+
+def test_checkpoint_format_shared_with_the_host_reader(sxl, tmp_path):
+    """A checkpoint the library writes reads back on the host with the same
+    arrays (paper_2303_03529_gb300.checkpoint); one the host writes from
+    them, with a new step counter, reads into a fresh context and continues
+    like the original."""
+    from paper_2303_03529_gb300 import checkpoint
+    w = wl.fe16()
+    a = _md_context(sxl, w, "fp64")
+    a.step(3, stats=False)
+    p1 = tmp_path / "lib.ckpt"
+    a.checkpoint_write(str(p1))
+    ck = checkpoint.read(p1)
+    R, V, nh, mu = a.get_state()
+    assert ck["md_step"] == 3 and ck["mu"] == mu and ck["n_atoms"] == w.n_atoms
+    np.testing.assert_array_equal(ck["R"], R.cpu().numpy())
+    np.testing.assert_array_equal(ck["V"], V.cpu().numpy())
+    np.testing.assert_array_equal(ck["nhist"], nh.cpu().numpy())
+    p2 = tmp_path / "host.ckpt"
+    checkpoint.write(p2, dict(ck, md_step=100))
+    b = sxl.Context(w.params, w.n_atoms, w.cell, "fp64", scf_keep_k0=1)
+    b.checkpoint_read(str(p2))
+    assert b.md_step() == 100
+    st_a, st_b = a.step(2), b.step(2)
+    assert np.array_equal(st_a, st_b)
+    a.close()
+    b.close()
