@@ -111,11 +111,16 @@ def scf(R, cell, n0, p, tol=1e-8, max_iter=200, rank=None, lin_mix=0.06,
 class XLBOMD:
     """State and time stepping of Eq. Integration."""
 
-    def __init__(self, R, V, cell, n_star, p, K0, mu=None, general_model=False):
+    def __init__(self, R, V, cell, n_star, p, K0, mu=None, general_model=False, recycle=False):
         """general_model: the non-orthogonal, l-resolved model of
-        oracle/general.py in place of the orthogonal per-atom one."""
+        oracle/general.py in place of the orthogonal per-atom one.
+        recycle: after the first evaluation, the kernel of each step is the
+        recycled-subspace variant over the previous step's directions
+        (kernel.krylov_kernel_subspace, a build choice, not the paper's)."""
         self.p = p
         self.general_model = general_model
+        self.recycle = recycle
+        self.Vrec = None
         self.cell = np.asarray(cell, dtype=np.float64)
         self.R = np.array(R, dtype=np.float64)
         self.V = np.array(V, dtype=np.float64)
@@ -141,7 +146,14 @@ class XLBOMD:
             self.E = energy.shadow_energy(self.dens, H0,
                                           model.repulsive_energy(self.R, self.cell, p))
         self.mu = self.dens.mu
-        self.Kf, self.kinfo = kernel.krylov_kernel(self.dens, self.K0, p.krylov_rank)
+        if self.recycle and self.Vrec is not None:
+            self.Kf, self.kinfo = kernel.krylov_kernel_subspace(
+                self.dens, self.K0, [self.Vrec[:, j] for j in range(self.Vrec.shape[1])],
+                p.krylov_rank)
+        else:
+            self.Kf, self.kinfo = kernel.krylov_kernel(self.dens, self.K0, p.krylov_rank)
+        if self.recycle:
+            self.Vrec = self.kinfo["V"]
 
     def accel(self):
         return self.F / (self.p.mass_amu * MVV_TO_EV)

@@ -263,3 +263,24 @@ def test_subspace_kernel_on_the_krylov_span_equals_the_krylov_kernel(dens16):
     ft = K0 @ d.residual()
     Kf_1, info_1 = kernel.krylov_kernel_subspace(d, K0, [2.0 * ft, -ft], rank=5)
     assert info_1["rank"] == 1
+
+
+def test_recycled_kernel_dynamics_match_the_krylov_kernel():
+    """40 sXL-BOMD steps of the 16-atom cell from its SCF point with the
+    recycled-subspace kernel stay on the same shadow surface as with the
+    Krylov construction: the same energy spread and residual within a small
+    factor, and trajectories that agree to far below the thermal scale
+    (both kernels approximate the same J^-1)."""
+    w = wl.fe16()
+    p = w.params
+    s = dynamics.scf(w.R, w.cell, w.n0, p, tol=1e-10)
+    runs = {}
+    for rec in (False, True):
+        md = dynamics.XLBOMD(w.R, w.V, w.cell, s["n"], p, s["K0"], mu=s["mu"], recycle=rec)
+        st = [md.step() for _ in range(40)]
+        runs[rec] = (np.array([x["Etot"] for x in st]), np.array([x["rms"] for x in st]), md.R)
+    (Ek, rk, Rk), (Er, rr, Rr) = runs[False], runs[True]
+    spread = lambda E: (E.max() - E.min()) / w.n_atoms
+    assert spread(Er) < 2.0 * spread(Ek) + 1e-7
+    assert rr.max() < 2.0 * rk.max() + 1e-6
+    assert np.abs(Rr - Rk).max() < 1e-4
