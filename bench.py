@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fe1024")
+    ap.add_argument("--config", default=None,
+                    help="a workload configuration file (JSON, paper_2303_03529_gb300/configs) "
+                         "in place of --workload")
     ap.add_argument("--precision", default="fp16", choices=["fp16", "bf16", "fp64"])
     ap.add_argument("--krylov", default="krylov", choices=["krylov", "recycled"],
                     help="xlbomd_step's kernel: the Krylov construction of Eq. mIJacobian, or "
@@ -207,6 +210,13 @@ def replica_throughput(steps_per_rank: int, world: int, max_seconds: float) -> f
     return world * steps_per_rank / max_seconds
 
 
+def load_workload(workload, args):
+    """The run's workload: a configuration file (--config) or a named one."""
+    if args.config:
+        return workload.load_config(args.config)
+    return workload.WORKLOADS[args.workload]()
+
+
 def prepare_state(sxl, w, precision, local, krylov_recycle=0):
     """Initial MD state: SCF from n = 0 with the Krylov kernel mixer and
     K0 = -I (outside the timed region), all history slots = n*.  The general
@@ -339,7 +349,7 @@ def run_ours(args):
         _build.build()
     if ws > 1:
         torch.distributed.barrier()
-    w = workload.WORKLOADS[args.workload]()
+    w = load_workload(workload, args)
     ctx, setup = prepare_state(sxl, w, args.precision, local,
                                1 if args.krylov == "recycled" else 0)
     stream = ctx.stream
@@ -620,7 +630,7 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2303_03529_gb300 import workload
-    w = workload.WORKLOADS[args.workload]()
+    w = load_workload(workload, args)
     t_start = time.perf_counter()
     st = OracleStep(w)
     for _ in range(args.warmup):

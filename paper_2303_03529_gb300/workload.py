@@ -100,6 +100,9 @@ class Workload:
     cell: np.ndarray       # (3,)
     params: ModelParams
     steps: int
+    # the make_cell arguments that regenerate R, V and n0 (see config())
+    recipe: Optional[dict] = None
+    shell_resolved_n0: bool = False
 
     @property
     def n_atoms(self) -> int:
@@ -166,8 +169,11 @@ def make_cell(ncell: int, *, seed: int, sigma: float = 0.05, a: float = 2.87,
     V = maxwell_velocities(rng, R.shape[0], params.mass_amu, T_K)
     n0 = initial_n(rng, R.shape[0], m0=m0, noise=noise)
     cell = np.full(3, ncell * a)
+    recipe = dict(ncell=int(ncell), seed=int(seed), sigma=float(sigma), a=float(a),
+                  T_K=float(T_K), m0=float(m0), noise=float(noise),
+                  vacancy_frac=float(vacancy_frac))
     return Workload(name=name, ncell=ncell, a=a, R=R, V=V, n0=n0, cell=cell,
-                    params=params, steps=steps)
+                    params=params, steps=steps, recipe=recipe)
 
 
 # The three single-GPU workloads of the hot path (16, 128 and 1024 atoms).
@@ -239,6 +245,7 @@ def fe16_general() -> Workload:
     w = fe16()
     w.params = general_model(w.params)
     w.n0 = shell_resolved_n(w.n0)
+    w.shell_resolved_n0 = True
     w.name = "fe16_bcc2x2x2_general"
     return w
 
@@ -248,6 +255,7 @@ def fe54_general() -> Workload:
     w = make_cell(3, seed=SEED_BASE + 6, name="fe54_bcc3x3x3_general",
                   params=general_model(ModelParams(krylov_rank=4)))
     w.n0 = shell_resolved_n(w.n0)
+    w.shell_resolved_n0 = True
     return w
 
 
@@ -256,6 +264,7 @@ def fe128_general() -> Workload:
     w = fe128()
     w.params = general_model(w.params)
     w.n0 = shell_resolved_n(w.n0)
+    w.shell_resolved_n0 = True
     w.name = "fe128_bcc4x4x4_general"
     return w
 
@@ -265,6 +274,7 @@ def fe1024_general() -> Workload:
     w = fe1024()
     w.params = general_model(w.params)
     w.n0 = shell_resolved_n(w.n0)
+    w.shell_resolved_n0 = True
     w.name = "fe1024_bcc8x8x8_general"
     return w
 
@@ -274,8 +284,78 @@ WORKLOADS = {"fe16": fe16, "fe128": fe128, "fe1024": fe1024, "fe2000": fe2000,
              "fe128_general": fe128_general, "fe1024_general": fe1024_general}
 
 
+# ---------------------------------------------------------------------------
+# JSON configurations: one file per workload, holding the parameter set (the
+# fields of sxl_params, one to one) and the seeded recipe of the cell.
+CONFIG_VERSION = 1
+
+
+def config(w: Workload, precision: Optional[str] = None) -> dict:
+    """The JSON-able configuration that regenerates w exactly: parameters,
+    the make_cell recipe (lattice, seeds, displacements, vacancies,
+    temperature, initial moments), the step count and, optionally, the
+    arithmetic form a run should use."""
+    if w.recipe is None:
+        raise ValueError("workload was not made by make_cell")
+    params = {k: (list(v) if isinstance(v, tuple) else v)
+              for k, v in dataclasses.asdict(w.params).items()}
+    out = {"version": CONFIG_VERSION, "name": w.name, "lattice": "bcc",
+           "cell": dict(w.recipe), "steps": int(w.steps),
+           "shell_resolved_n0": bool(w.shell_resolved_n0), "params": params}
+    if precision is not None:
+        out["precision"] = precision
+    return out
+
+
+def from_config(cfg: dict) -> Workload:
+    """The workload a configuration describes (inverse of config())."""
+    if cfg.get("version") != CONFIG_VERSION or cfg.get("lattice", "bcc") != "bcc":
+        raise ValueError("unsupported workload configuration")
+    fields = {f.name for f in dataclasses.fields(ModelParams)}
+    unknown = set(cfg["params"]) - fields
+    if unknown:
+        raise ValueError(f"unknown parameters {sorted(unknown)}")
+    params = ModelParams(**{k: (tuple(v) if isinstance(v, list) else v)
+                            for k, v in cfg["params"].items()})
+    c = dict(cfg["cell"])
+    ncell = c.pop("ncell")
+    w = make_cell(ncell, params=params, name=cfg["name"], steps=int(cfg.get("steps", 0)), **c)
+    if cfg.get("shell_resolved_n0"):
+        w.n0 = shell_resolved_n(w.n0)
+        w.shell_resolved_n0 = True
+    return w
+
+
+def load_config(path) -> Workload:
+    import json
+    with open(path) as f:
+        return from_config(json.load(f))
+
+
+def write_configs(directory) -> list:
+    """Writes <name>.json for every named workload into directory."""
+    import json
+    import os
+    os.makedirs(directory, exist_ok=True)
+    paths = []
+    for key, make in WORKLOADS.items():
+        path = os.path.join(directory, f"{key}.json")
+        with open(path, "w") as f:
+            json.dump(config(make()), f, indent=1)
+            f.write("\n")
+        paths.append(path)
+    return paths
+
+
 def random_direction(n_atoms: int, seed: int) -> np.ndarray:
     """Seeded unit vector in R^{2 N_at} (a perturbation direction v)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     v = rng.normal(size=2 * n_atoms)
     return v / np.linalg.norm(v)
+
+
+if __name__ == "__main__":
+    import sys
+    for p in write_configs(sys.argv[1] if len(sys.argv) > 1 else
+                           __file__.rsplit("/", 1)[0] + "/configs"):
+        print(p)
