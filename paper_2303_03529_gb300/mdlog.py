@@ -10,7 +10,9 @@ the wall time per step:
 `step_record` builds one record from the library's per-step statistics row
 [E_tot (eV), T (K), RMS(q - n), mu (eV)] and the charges and spins q of the
 evaluation (up block, then down block; per atom, or per atom and shell).
-`run` steps a context and appends records to a file.
+`run` steps a context and appends records to a file.  `spin_flip_events`
+scans records for the discontinuities a spin flip leaves (Sec. IV: the
+residual jumps and the moments change abruptly).
 """
 from __future__ import annotations
 
@@ -65,3 +67,21 @@ def run(ctx, nsteps: int, path, every: int = 1, spins: bool = True):
             f.write(json.dumps(rec) + "\n")
             out.append(rec)
     return out
+
+
+def spin_flip_events(records, rms_factor: float = 10.0, moment_jump: float = 0.5):
+    """Steps at which a spin flip shows in a sequence of records: the
+    residual RMS(q - n) grows by more than rms_factor over the previous
+    record, or the total or the largest atomic moment changes by more than
+    moment_jump (electrons) between consecutive records.  Returns a list of
+    (step, reason) pairs."""
+    events = []
+    for prev, cur in zip(records, records[1:]):
+        step = cur["step"]
+        if prev["rms_q_minus_n"] > 0 and cur["rms_q_minus_n"] > rms_factor * prev["rms_q_minus_n"]:
+            events.append((step, "residual jump"))
+        for key in ("m_total", "m_abs_max"):
+            if key in cur and key in prev and abs(cur[key] - prev[key]) > moment_jump:
+                events.append((step, f"{key} jump"))
+    return events
+

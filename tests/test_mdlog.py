@@ -61,3 +61,14 @@ def test_run_writes_one_line_per_block(tmp_path):
     assert lines[0]["m_total"] == pytest.approx(1.4)
     with pytest.raises(ValueError):
         mdlog.run(_FakeContext(), 3, path, every=0)
+
+
+def test_spin_flip_events():
+    def rec(step, rms, mt, ma):
+        return {"step": step, "rms_q_minus_n": rms, "m_total": mt, "m_abs_max": ma}
+    quiet = [rec(i, 1e-4, 32.0, 2.1) for i in range(5)]
+    assert mdlog.spin_flip_events(quiet) == []
+    flip = quiet + [rec(5, 3e-3, 30.0, 2.1), rec(6, 2e-4, 30.0, 2.1)]
+    ev = mdlog.spin_flip_events(flip)
+    assert (5, "residual jump") in ev and (5, "m_total jump") in ev
+    assert all(s == 5 for s, _ in ev)
