@@ -11,9 +11,9 @@ the wall time per step:
 [E_tot (eV), T (K), RMS(q - n), mu (eV)] and the charges and spins q of the
 evaluation (up block, then down block; per atom, or per atom and shell).
 `run` steps a context and appends records to a file.  `spin_flip_events`
-scans records for the discontinuities a spin flip leaves (the paper's
-Summary and Discussion names such flips as a limit of collinear spins: the
-residual jumps and the moments change abruptly).
+scans records for the marks a spin flip leaves: the residual jumps and the
+moments change abruptly (the paper's Summary and Discussion names such
+flips, a discontinuity of the potential, as a limit of collinear spins).
 """
 from __future__ import annotations
 
